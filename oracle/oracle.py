@@ -1,0 +1,240 @@
+"""ctypes wrapper of the C oracle (test infrastructure only).
+
+The shared library ``oracle/liboracle.so`` is compiled by
+``__graft_entry__.build()`` (or ``build_oracle()`` below) with contraction
+off, so every float expression is evaluated exactly as written.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Dict, Optional
+
+import numpy as np
+
+from paper_2402_13259_gb300.workloads import ARR_NONE, Network
+
+__all__ = [
+    "build_oracle", "lib", "simulate", "num_steps", "stats_split", "philox", "map_f32",
+    "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
+    "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
+    "BACKWARD", "FORWARD",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.environ.get("EULER_ORACLE_SO") or os.path.join(HERE, "liboracle.so")
+SOURCES = [os.path.join(HERE, "euler_oracle.c")]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-Wall", "-Wno-unused-function"]
+
+BACKWARD, FORWARD = 0, 1
+
+COUNTER_NAMES = [
+    "units", "philox_blocks", "uniforms",
+    "pois_inv", "pois_inv_iters", "pois_ptrs", "pois_ptrs_iters", "pois_ptrs_logtests",
+    "bin_inv", "bin_inv_iters", "bin_btrs", "bin_btrs_iters", "bin_btrs_logtests",
+    "gamma_small", "gamma_small_logs", "gamma_mt", "gamma_mt_iters", "normal_iters",
+    "dep_le_m", "dep_t_gt_h", "dep_t_le_h", "route_binomials", "gather_edges",
+]
+
+
+def build_oracle(force: bool = False) -> str:
+    if os.environ.get("EULER_ORACLE_SO"):
+        return SO_PATH  # a prebuilt variant (used by the mutation test)
+    newest = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "euler_oracle.h")])
+    if force or not os.path.exists(SO_PATH) or os.path.getmtime(SO_PATH) < newest:
+        tmp = SO_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *SOURCES, "-lm"])
+        os.replace(tmp, SO_PATH)
+    return SO_PATH
+
+
+class _Net(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("prob", C.c_void_p),
+        ("servers", C.c_void_p), ("mu", C.c_void_p), ("arr_kind", C.c_int32),
+        ("w", C.c_void_p), ("a", C.c_double), ("b", C.c_double), ("period", C.c_double),
+        ("phase", C.c_double), ("table", C.c_void_p), ("table_len", C.c_int32),
+        ("tab_dt", C.c_double), ("N0", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        L = C.CDLL(SO_PATH)
+        L.eo_simulate.restype = C.c_int
+        L.eo_simulate.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
+                                  C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]
+        L.eo_num_steps.restype = C.c_int64
+        L.eo_num_steps.argtypes = [C.c_double, C.c_double]
+        L.eo_set_cap.restype = C.c_int32
+        L.eo_set_cap.argtypes = [C.c_int32]
+        L.eo_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.eo_map_f32.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_int64]
+        L.eo_draw_poisson.argtypes = [C.c_float, C.c_uint64, C.c_int64, C.c_void_p]
+        L.eo_draw_binomial.argtypes = [C.c_int32, C.c_float, C.c_uint64, C.c_int64, C.c_void_p]
+        L.eo_draw_gamma.argtypes = [C.c_int32, C.c_float, C.c_uint64, C.c_int64, C.c_void_p]
+        L.eo_draw_normal.argtypes = [C.c_uint64, C.c_int64, C.c_void_p]
+        L.eo_draw_departure.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                        C.c_int64, C.c_void_p]
+        L.eo_draw_route.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_uint64, C.c_int64,
+                                    C.c_void_p]
+        L.eo_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                  C.c_int64, C.c_void_p]
+        L.eo_counters_get.argtypes = [C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _make_net(net: Network):
+    keep = []
+    a = net.arrivals
+    s = _Net()
+    s.n = net.n
+    for name in ("row_ptr", "col", "prob", "servers", "mu"):
+        arr = getattr(net, name)
+        if arr.size == 0:
+            arr = np.zeros(1, dtype=arr.dtype)
+        keep.append(arr)
+        setattr(s, name, _ptr(arr))
+    s.arr_kind = a.kind
+    if a.w is not None:
+        keep.append(a.w)
+        s.w = _ptr(a.w)
+    s.a, s.b, s.period, s.phase = a.a, a.b, a.period, a.phase
+    if a.table is not None:
+        keep.append(a.table)
+        s.table = _ptr(a.table)
+        s.table_len = a.table.shape[0]
+    s.tab_dt = a.tab_dt
+    if net.N0 is not None:
+        keep.append(net.N0)
+        s.N0 = _ptr(net.N0)
+    return s, keep
+
+
+def num_steps(dt: float, T: float) -> int:
+    return int(lib().eo_num_steps(dt, T))
+
+
+def stats_split(stats: np.ndarray, n: int, R: int) -> Dict[str, np.ndarray]:
+    st = stats[: 5 * n].reshape(n, 5)
+    rp = stats[5 * n: 5 * n + 4 * R].reshape(R, 4)
+    nk = stats[5 * n + 4 * R: 6 * n + 4 * R]
+    return {"station": st, "rep": rp, "NK": nk}
+
+
+def simulate(net: Network, scheme: int, dt: float, T: float, R: int, seed: int,
+             rep_begin: int = 0, trace: bool = False, expect_ok: bool = True):
+    """Run the oracle; returns dict with 'stats' (flat int64), split views, and
+    optionally 'N', 'D', 'A' traces of shape [K, n, R]."""
+    L = lib()
+    s, keep = _make_net(net)
+    n = net.n
+    stats = np.zeros(6 * n + 4 * R, dtype=np.int64)
+    K = num_steps(dt, T)
+    tr = {}
+    if trace:
+        for k in ("N", "D", "A"):
+            tr[k] = np.zeros((K, n, R), dtype=np.int32)
+    rc = L.eo_simulate(C.byref(s), scheme, dt, T, R, seed, rep_begin, _ptr(stats),
+                       _ptr(tr.get("N")), _ptr(tr.get("D")), _ptr(tr.get("A")))
+    del keep
+    if expect_ok and rc != 0:
+        raise RuntimeError(f"oracle eo_simulate failed with code {rc}")
+    out = {"rc": rc, "stats": stats, "K": K}
+    out.update(stats_split(stats, n, R))
+    out.update(tr)
+    return out
+
+
+def set_cap(cap: int) -> int:
+    return int(lib().eo_set_cap(cap))
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().eo_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+_FN = {"exp": 0, "log": 1, "expm1": 2, "log1p": 3}
+
+
+def map_f32(fn: str, x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    lib().eo_map_f32(_FN[fn], _ptr(x), _ptr(y), x.size)
+    return y
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError(f"oracle sampler returned {rc}")
+
+
+def draw_poisson(lam: float, seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.int32)
+    _check(lib().eo_draw_poisson(lam, seed, count, _ptr(out)))
+    return out
+
+
+def draw_binomial(n: int, p: float, seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.int32)
+    _check(lib().eo_draw_binomial(n, p, seed, count, _ptr(out)))
+    return out
+
+
+def draw_gamma(k: int, rate: float, seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.float32)
+    _check(lib().eo_draw_gamma(k, rate, seed, count, _ptr(out)))
+    return out
+
+
+def draw_normal(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.float32)
+    _check(lib().eo_draw_normal(seed, count, _ptr(out)))
+    return out
+
+
+def draw_departure(x: int, m: int, mu: float, h: float, seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.int32)
+    _check(lib().eo_draw_departure(x, m, mu, h, seed, count, _ptr(out)))
+    return out
+
+
+def draw_route(D: int, prob, seed: int, count: int) -> np.ndarray:
+    p = np.ascontiguousarray(prob, dtype=np.float64)
+    deg = p.size
+    out = np.empty((count, deg + 1), dtype=np.int32)
+    _check(lib().eo_draw_route(D, deg, _ptr(p if deg else np.zeros(1)), seed, count, _ptr(out)))
+    return out
+
+
+def uniforms(seed: int, purpose: int, station: int, step: int, rep: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.float32)
+    lib().eo_uniforms(seed, purpose, station, step, rep, count, _ptr(out))
+    return out
+
+
+def counters_reset():
+    lib().eo_counters_reset()
+
+
+def counters() -> Dict[str, int]:
+    out = np.zeros(len(COUNTER_NAMES), dtype=np.int64)
+    lib().eo_counters_get(_ptr(out))
+    return dict(zip(COUNTER_NAMES, (int(v) for v in out)))

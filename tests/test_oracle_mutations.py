@@ -1,0 +1,77 @@
+"""The pins of test_oracle_pins.py must reject plausible slips in the oracle.
+
+Each case plants one mistake in a copy of oracle/euler_oracle.c, builds it to
+a temporary library and runs the pin suite against it in a subprocess; the
+suite must fail.  Nothing here touches a GPU.
+"""
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "euler_oracle.c")
+
+MUTANTS = [
+    # Algorithm 1, T > h branch: Binomial(x - m - 1, h/T) -> Binomial(x - m, h/T)
+    ("alg1_tail_count", "return sample_binomial(x - m - 1, h / T, st, err);",
+     "return sample_binomial(x - m, h / T, st, err);"),
+    # Algorithm 1, T <= h branch: the x - m already served are dropped
+    ("alg1_served_dropped", "return (x - m) + sample_binomial(m, p, st, err);",
+     "return sample_binomial(m, p, st, err);"),
+    # Lemma 1: Erlang rate m*mu written as mu
+    ("erlang_rate", "float rate = (float)m * mu;", "float rate = mu;"),
+    # Lemma 1(1): the x <= m test off by one.  (x < m would be no mistake: at
+    # x = m the Erlang branch has T = 0 and reduces to the same binomial law.)
+    ("branch_off_by_one", "if (x <= m) {\n    CNT(EOC_DEP_LE_M);", "if (x <= m + 1) {\n    CNT(EOC_DEP_LE_M);"),
+    # routing: unconditional p_e used in the sequential binomials
+    ("route_unconditional", "double q = suffix > 0.0 ? net->prob[e] / suffix : 0.0;",
+     "double q = net->prob[e];"),
+    # backward scheme: departures drawn after adding the step's arrivals
+    ("backward_order", "D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err);",
+     "D[i] = departure(N[i] + (int32_t)(lam_t[i] > 0.0f ? 1 : 0), net->servers[i], mu_f[i], h_f, p0[i], &svc, &err);"),
+    # forward scheme: internal arrivals left out of the departure input
+    ("forward_missing_ain", "int64_t y = (int64_t)N[i] + A[i] + ain;", "int64_t y = (int64_t)N[i] + A[i];"),
+    # arrival integral: sign of the sinusoid term flipped
+    ("lambda_sign", "(cos(om * t0 + net->phase) - cos(om * t1 + net->phase))",
+     "(cos(om * t1 + net->phase) - cos(om * t0 + net->phase))"),
+    # binomial inversion recursion: (n - k) -> (n - k - 1)
+    ("binom_inv_recursion", "pk = ((pk * (float)(n - k)) * r) * rinv_tab[k + 1];",
+     "pk = ((pk * (float)(n - k - 1)) * r) * rinv_tab[k + 1];"),
+    # PTRS constant slip
+    ("ptrs_constant", "float a = -0.059f + 0.02483f * b;", "float a = 0.059f + 0.02483f * b;"),
+    # BTRS: mode term dropped from the acceptance test
+    ("btrs_mode", "if (lv <= logpmf_binom(k, n, p, q) - lpm) return k;",
+     "if (lv <= logpmf_binom(k, n, p, q)) return k;"),
+    # statistics: busy servers counted as customers
+    ("stat_busy", "ss[1] += N[i] < net->servers[i] ? N[i] : net->servers[i];", "ss[1] += N[i];"),
+    # Philox: a Weyl key constant slip
+    ("philox_weyl", "#define PHILOX_W1 0xBB67AE85u", "#define PHILOX_W1 0xBB67AE84u"),
+    # exp: a Taylor coefficient slip
+    ("exp_coeff", "p = fmaf(p, r, (float)(1.0 / 6.0));", "p = fmaf(p, r, (float)(1.0 / 7.0));"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_mutant(name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    tmp = tempfile.mkdtemp(prefix=f"mut_{name}_")
+    try:
+        cfile = os.path.join(tmp, "euler_oracle.c")
+        with open(cfile, "w") as f:
+            f.write(src.replace(old, new))
+        shutil.copy(os.path.join(ROOT, "oracle", "euler_oracle.h"), tmp)
+        so = os.path.join(tmp, "liboracle.so")
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", so, cfile, "-lm"])
+        env = dict(os.environ, EULER_ORACLE_SO=so)
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)

@@ -1,0 +1,473 @@
+"""Pins of the CPU oracle against facts the paper and mathematics fix.
+
+Each test states what it pins.  A plausible slip in the oracle -- a dropped
+term, a wrong branch of Algorithm 1, the backward/forward ordering swapped,
+a transposed routing index, a wrong arrival integral -- fails at least one:
+
+* Philox4x32-10 against the published known-answer vectors;
+* float math against numpy's double-precision functions (ulp bounds);
+* every sampler against its exact law (chi-square / KS, fixed seeds);
+* GenerateDeparture (Lemma 1, Algorithm 1) against the exact pure-death
+  transition law exp(Q h) of the proof of Lemma 2, by brute force;
+* routing against the multinomial pmf (Sec. 2.2);
+* the worked 2-node tandem example of Sec. 2.3;
+* the infinite-server closed form (Lemma 1(1) + Poisson thinning) of both
+  schemes on a random DAG with time-varying arrivals;
+* the exact single-station distribution by brute-force convolution;
+* Argument 2 and Argument 3 (Sec. 4.1), Theorem 1's steady-state bracketing
+  of the Erlang-C mean and gap lambda*h, Theorem 2's per-node gap;
+* the arrival integral of Sec. 2.1.1 and the bookkeeping invariants.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.linalg import expm
+
+from paper_2402_13259_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _chi2_p(obs, expected, min_exp=10.0):
+    obs = np.asarray(obs, dtype=np.float64)
+    expected = np.asarray(expected, dtype=np.float64)
+    m = expected > min_exp
+    # pool everything below the threshold into one cell
+    o = np.concatenate([obs[m], [obs[~m].sum()]])
+    e = np.concatenate([expected[m], [expected[~m].sum()]])
+    keep = e > 0
+    o, e = o[keep], e[keep]
+    c = ((o - e) ** 2 / e).sum()
+    df = max(len(o) - 1, 1)
+    return stats.chi2.sf(c, df)
+
+
+# ---------------------------------------------------------------------------
+# Random numbers and float math
+# ---------------------------------------------------------------------------
+def test_philox_known_answers(orc):
+    """Philox4x32-10 reproduces the Random123 known-answer vectors."""
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            lhs, rhs = line.split("->")
+            v = [int(t, 16) for t in lhs.split()]
+            want = [int(t, 16) for t in rhs.split()]
+            got = orc.philox(v[:4], v[4:6])
+            assert [int(x) for x in got] == want
+            n += 1
+    assert n == 3
+
+
+def test_uniform_mapping(orc):
+    """Uniforms are odd multiples of 2^-24 in (0,1), built from consecutive
+    Philox words of the stream's counter blocks."""
+    u = orc.uniforms(seed=0x1234_5678_9ABC, purpose=1, station=7, step=3, rep=11, count=8)
+    words = np.concatenate([
+        orc.philox([(1 << 24) | b, 7, 3, 11], [0x5678_9ABC, 0x1234]) for b in range(2)])
+    want = (((words >> 9) << 1) | 1).astype(np.float64) * 2.0 ** -24
+    assert np.array_equal(u.astype(np.float64), want)
+    big = orc.uniforms(seed=5, purpose=0, station=0, step=1, rep=0, count=1_000_000)
+    assert big.min() >= 2.0 ** -24 and big.max() <= 1 - 2.0 ** -24
+    assert abs(big.mean() - 0.5) < 5 * math.sqrt(1 / 12 / big.size)
+    assert stats.kstest(big.astype(np.float64), "uniform").pvalue > 1e-4
+
+
+def _ulps(y, ref):
+    sp = np.abs(np.spacing(ref.astype(np.float32))).astype(np.float64)
+    return np.abs(y.astype(np.float64) - ref) / sp
+
+
+def test_float_math_ulp(orc):
+    """The oracle's own exp/log/expm1/log1p stay within a few ulp of the
+    correctly rounded values (numpy float64 as reference)."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-87, 88.7, 500_000), rng.uniform(-1, 1, 200_000)]).astype(np.float32)
+    assert _ulps(orc.map_f32("exp", x), np.exp(x.astype(np.float64))).max() <= 1.0
+    x = np.exp(rng.uniform(-87, 88, 500_000)).astype(np.float32)
+    x = np.concatenate([x, rng.uniform(0.5, 2.0, 200_000).astype(np.float32)])
+    assert _ulps(orc.map_f32("log", x), np.log(x.astype(np.float64))).max() <= 1.0
+    x = np.concatenate([rng.uniform(-20, 5, 300_000), -np.exp(rng.uniform(-30, 0, 300_000)),
+                        np.exp(rng.uniform(-30, 0, 300_000))]).astype(np.float32)
+    assert _ulps(orc.map_f32("expm1", x), np.expm1(x.astype(np.float64))).max() <= 4.0
+    x = np.concatenate([rng.uniform(-0.9999, 5, 300_000), -np.exp(rng.uniform(-30, -1e-4, 300_000)),
+                        np.exp(rng.uniform(-30, 3, 300_000))]).astype(np.float32)
+    assert _ulps(orc.map_f32("log1p", x), np.log1p(x.astype(np.float64))).max() <= 4.0
+    special = np.array([0.0, 1.0, -1.0, 100.0, -120.0], dtype=np.float32)
+    y = orc.map_f32("exp", special)
+    assert y[0] == 1.0 and y[3] == np.inf and y[4] == 0.0
+    assert orc.map_f32("log", np.array([1.0], np.float32))[0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Samplers against their exact laws
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lam", [1e-3, 0.4, 3.0, 9.99, 10.0, 25.0, 180.0, 5000.0])
+def test_poisson_sampler(orc, lam):
+    """Poisson(lam): inversion (lam < 10) and PTRS (lam >= 10) follow the pmf."""
+    N = 400_000
+    x = orc.draw_poisson(lam, 101, N)
+    lam32 = float(np.float32(lam))
+    hi = int(stats.poisson.isf(1e-9, lam32)) + 2
+    obs = np.bincount(x, minlength=hi + 1)
+    obs = np.concatenate([obs[:hi], [obs[hi:].sum()]])
+    pm = stats.poisson.pmf(np.arange(hi), lam32)
+    pm = np.concatenate([pm, [stats.poisson.sf(hi - 1, lam32)]])
+    assert _chi2_p(obs, pm * N) > 1e-4
+    assert abs(x.mean() - lam32) < 5 * math.sqrt(lam32 / N)
+
+
+@pytest.mark.parametrize("n,p", [(1, 0.3), (7, 0.3), (100, 0.05), (30, 0.5), (1000, 0.011),
+                                 (200, 0.3), (100000, 0.004), (50, 0.9), (700, 0.97),
+                                 (2_000_000, 0.45)])
+def test_binomial_sampler(orc, n, p):
+    """Binomial(n, p): inversion (np < 10), BTRS (np >= 10), symmetric p > 1/2."""
+    N = 300_000
+    x = orc.draw_binomial(n, p, 202, N)
+    p32 = float(np.float32(p))
+    lo = int(stats.binom.ppf(1e-9, n, p32))
+    hi = int(stats.binom.isf(1e-9, n, p32)) + 1
+    ks = np.arange(lo, hi + 1)
+    obs = np.bincount(np.clip(x, lo, hi) - lo, minlength=len(ks))
+    pm = stats.binom.pmf(ks, n, p32)
+    pm[0] = stats.binom.cdf(lo, n, p32)
+    pm[-1] = stats.binom.sf(hi - 1, n, p32)
+    assert _chi2_p(obs, pm * N) > 1e-4
+    assert abs(x.mean() - n * p32) < 5 * math.sqrt(n * p32 * (1 - p32) / N) + 1e-9
+
+
+def test_binomial_degenerate(orc):
+    """Bin(0, p) = 0, Bin(n, 0) = 0, Bin(n, 1) = n (Appendix A's convention)."""
+    assert (orc.draw_binomial(0, 0.5, 1, 100) == 0).all()
+    assert (orc.draw_binomial(10, 0.0, 1, 100) == 0).all()
+    assert (orc.draw_binomial(10, 1.0, 1, 100) == 10).all()
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 9, 50, 3000])
+def test_erlang_sampler(orc, k):
+    """Erlang(k, rate): product-of-uniforms (k <= 8) and Marsaglia-Tsang."""
+    g = orc.draw_gamma(k, 2.5, 303, 200_000).astype(np.float64)
+    assert stats.kstest(g, stats.gamma(k, scale=1 / 2.5).cdf).pvalue > 1e-4
+
+
+def test_normal_sampler(orc):
+    z = orc.draw_normal(404, 300_000).astype(np.float64)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+
+
+def _pure_death_law(x, m, mu, h):
+    """P(D = d) for the pure departure process from x customers (generator
+    q_{y,y-1} = min(y, m) mu, proof of Lemma 2), via the matrix exponential."""
+    Q = np.zeros((x + 1, x + 1))
+    for y in range(1, x + 1):
+        r = min(y, m) * mu
+        Q[y, y - 1] = r
+        Q[y, y] = -r
+    return expm(Q * h)[x][::-1]
+
+
+@pytest.mark.parametrize("x,m,mu,h", [
+    (0, 3, 1.0, 0.5), (5, 8, 1.0, 0.3), (8, 8, 0.7, 0.5), (9, 8, 0.7, 0.5), (12, 3, 2.0, 0.5),
+    (40, 3, 1.0, 0.5), (40, 8, 0.5, 2.0), (30, 1, 1.0, 0.05), (25, 4, 3.0, 1.0),
+    (60, 5, 0.2, 0.1), (35, 30, 1.0, 0.8)])
+def test_departure_exact_law(orc, x, m, mu, h):
+    """GenerateDeparture (Algorithm 1) samples the exact law of Lemma 1."""
+    N = 400_000
+    d = orc.draw_departure(x, m, mu, h, 505, N)
+    law = _pure_death_law(x, m, float(np.float32(mu)), float(np.float32(h)))
+    obs = np.bincount(d, minlength=x + 1)
+    assert d.min() >= 0 and d.max() <= x
+    assert _chi2_p(obs, law * N) > 1e-4
+
+
+def test_route_multinomial(orc):
+    """Sequential conditional binomials give Multinomial(D, (p, p_exit))."""
+    prob = np.array([0.2, 0.45, 0.15])
+    D = 9
+    N = 200_000
+    out = orc.draw_route(D, prob, 606, N)
+    assert (out.sum(axis=1) == D).all() and (out >= 0).all()
+    full = np.concatenate([prob, [1 - prob.sum()]])
+    keys = out @ np.array([1, 10, 100, 1000])
+    uniq, cnt = np.unique(keys, return_counts=True)
+    cells = [(u % 10, (u // 10) % 10, (u // 100) % 10, u // 1000) for u in uniq]
+    exp = np.array([stats.multinomial.pmf(c, D, full) for c in cells]) * N
+    # cells never drawn: their expected mass is the complement
+    rest = N - exp.sum()
+    assert _chi2_p(np.concatenate([cnt, [0]]), np.concatenate([exp, [max(rest, 0)]])) > 1e-4
+    # exit-free row: everything routed, nothing exits
+    out2 = orc.draw_route(7, np.array([0.3, 0.7]), 1, 1000)
+    assert (out2[:, 2] == 0).all() and (out2[:, :2].sum(axis=1) == 7).all()
+
+
+# ---------------------------------------------------------------------------
+# Schemes
+# ---------------------------------------------------------------------------
+def _tandem2(mu, servers, lam, dt):
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, 1.0)])
+    arr = W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([lam, 0.0]), a=1.0, b=0.0)
+    return W.Network(2, row_ptr, col, prob, np.array(servers), np.array(mu, dtype=float), arr)
+
+
+def test_worked_example_tandem(orc):
+    """Sec. 2.3: one customer arriving in (0, h) with both service times below h
+    gives (N_0, N_h, N_2h, N_3h) = (0,1,1,0) backward and (0,0,0,0) forward.
+    With mu h = 100 every in-service customer finishes within the step, so the
+    schemes are deterministic given the arrivals; replications with exactly
+    one arrival in step 1 and none in steps 2-3 realise the example."""
+    dt = 0.01
+    net = _tandem2([1e4, 1e4], [10, 10], 50.0, dt)
+    R = 2000
+    b = orc.simulate(net, orc.BACKWARD, dt, 3 * dt, R, 7, trace=True)
+    f = orc.simulate(net, orc.FORWARD, dt, 3 * dt, R, 7, trace=True)
+    A = b["A"].sum(axis=1)  # [K, R]
+    assert np.array_equal(A, f["A"].sum(axis=1))  # common random numbers for arrivals
+    sel = (A[0] == 1) & (A[1] == 0) & (A[2] == 0)
+    assert sel.sum() > 50
+    tb = b["N"].sum(axis=1)[:, sel]
+    tf = f["N"].sum(axis=1)[:, sel]
+    assert (tb[0] == 1).all() and (tb[1] == 1).all() and (tb[2] == 0).all()
+    assert (tf == 0).all()
+    # per-node positions in the backward scheme: node 1 at h, node 2 at 2h
+    assert (b["N"][0, 0, sel] == 1).all() and (b["N"][1, 1, sel] == 1).all()
+
+
+def _inf_server_means(net, scheme, dt, K):
+    """Exact means when no station ever queues (Lemma 1(1) + thinning):
+    backward m_i' = e^{-mu_i h} m_i + L_i + sum_k p_ki (1-e^{-mu_k h}) m_k;
+    forward (flow order) y_i = m_i + L_i + sum_k p_ki (1-e^{-mu_k h}) y_k,
+    m_i' = e^{-mu_i h} y_i."""
+    n = net.n
+    a = net.arrivals
+    om = 2 * math.pi / a.period
+    stay = np.exp(-net.mu * dt)
+    m = np.zeros(n) if net.N0 is None else net.N0.astype(float)
+    out = np.zeros((K, n))
+    for tau in range(1, K + 1):
+        t0, t1 = (tau - 1) * dt, tau * dt
+        L = a.w * a.a * ((t1 - t0) + a.b * (math.cos(om * t0 + a.phase) - math.cos(om * t1 + a.phase)) / om)
+        if scheme == 0:
+            new = stay * m + L
+            for k in range(n):
+                for e in range(net.row_ptr[k], net.row_ptr[k + 1]):
+                    new[net.col[e]] += net.prob[e] * (1 - stay[k]) * m[k]
+            m = new
+        else:
+            y = m + L
+            for k in range(n):  # stations are numbered in flow order
+                for e in range(net.row_ptr[k], net.row_ptr[k + 1]):
+                    y[net.col[e]] += net.prob[e] * (1 - stay[k]) * y[k]
+            m = stay * y
+        out[tau - 1] = m
+    return out
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_infinite_server_closed_form(orc, scheme):
+    """With m_i above any reachable count both schemes keep independent Poisson
+    counts whose means follow the exact linear recursions above: checks the
+    step ordering of Algorithms 2/3, routing indices and arrival integrals."""
+    rng = np.random.default_rng(77)
+    net = W.random_small_dag(rng, 7, max_deg=3, ext_frac=0.6, lam_scale=20.0)
+    net.servers[:] = 1_000_000
+    dt, K, R = 0.05, 40, 20000
+    res = orc.simulate(net, scheme, dt, K * dt, R, 31, trace=True)
+    want = _inf_server_means(net, scheme, dt, K)
+    mean = res["N"].mean(axis=2)
+    var = res["N"].var(axis=2)
+    ok = want > 0.05
+    z = (mean[ok] - want[ok]) / np.sqrt(want[ok] / R)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    ratio = (var[ok] / want[ok]).mean()
+    assert abs(ratio - 1.0) < 0.02, ratio
+    tot = res["N"].sum(axis=1)[-1]
+    assert abs(tot.var() / tot.mean() - 1.0) < 0.06
+
+
+def _single_exact(m, mu, lam, h, N0, K, scheme, smax=90):
+    G = np.zeros((smax + 1, smax + 1))
+    for x in range(smax + 1):
+        law = _pure_death_law(x, m, mu, h)  # P(D = d)
+        for d in range(x + 1):
+            G[x, x - d] = law[d]
+    a = stats.poisson.pmf(np.arange(smax + 1), lam * h)
+    P = np.zeros(smax + 1)
+    P[N0] = 1.0
+    out = []
+    for _ in range(K):
+        if scheme == 0:
+            P = np.convolve(P @ G, a)[: smax + 1]
+        else:
+            P = np.convolve(P, a)[: smax + 1] @ G
+        out.append(P.copy())
+    return out
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_single_station_exact_distribution(orc, scheme):
+    """Brute force: backward N_t = G_h(N_{t-1}) + A_t, forward N_t =
+    G_h(N_{t-1} + A_t) (Sec. 2.1.3), distribution propagated exactly."""
+    m, mu, lam, h, N0, K = 2, 1.0, 3.0, 0.5, 1, 4
+    run = W.single_station(m, mu, lam, h, K * h, 200_000, 41, N0=N0)
+    res = orc.simulate(run.net, scheme, h, K * h, run.R, run.seed, trace=True)
+    exact = _single_exact(m, float(np.float32(mu)), lam, float(np.float32(h)), N0, K, scheme)
+    for t in range(K):
+        obs = np.bincount(res["N"][t, 0], minlength=91)[:91]
+        assert _chi2_p(obs, exact[t] * run.R) > 1e-4
+
+
+def test_argument3_identity(orc):
+    """Argument 3: E[N^b_t] - E[N^f_t] = E[D^f_t] <= m mu h for every t (idle
+    start, time-varying arrivals)."""
+    m, mu, h, K, R = 5, 1.0, 0.2, 30, 40000
+    run = W.single_station(m, mu, 4.0, h, K * h, R, 51, b=0.5, period=3.0)
+    b = orc.simulate(run.net, 0, h, K * h, R, 51, trace=True)
+    f = orc.simulate(run.net, 1, h, K * h, R, 51, trace=True)
+    diff = b["N"][:, 0, :].astype(np.int64) - f["N"][:, 0, :] - f["D"][:, 0, :]
+    z = diff.mean(axis=1) / (diff.std(axis=1) / math.sqrt(R) + 1e-12)
+    assert np.abs(z).max() < 5.0
+    assert (f["D"][:, 0, :].mean(axis=1) <= m * mu * h + 0.02).all()
+
+
+def test_argument2_identity(orc):
+    """Argument 2: N^b_t has the law of N^f_{t-1} + A_t (independent samples)."""
+    m, mu, h, K, R = 3, 1.2, 0.3, 12, 60000
+    run = W.single_station(m, mu, 3.0, h, K * h, R, 61)
+    b = orc.simulate(run.net, 0, h, K * h, R, 61, rep_begin=0, trace=True)
+    f = orc.simulate(run.net, 1, h, K * h, R, 61, rep_begin=R, trace=True)
+    for t in (1, 4, 11):
+        xb = b["N"][t, 0]
+        xf = f["N"][t - 1, 0] + f["A"][t, 0]
+        top = max(xb.max(), xf.max()) + 1
+        cb, cf = np.bincount(xb, minlength=top), np.bincount(xf, minlength=top)
+        keep = (cb + cf) > 20
+        table = np.stack([np.append(cb[keep], cb[~keep].sum()), np.append(cf[keep], cf[~keep].sum())])
+        table = table[:, table.sum(axis=0) > 0]
+        assert stats.chi2_contingency(table)[1] > 1e-4
+
+
+def _erlang_c_mean(m, lam, mu):
+    a = lam / mu
+    rho = a / m
+    top = a ** m / math.factorial(m) / (1 - rho)
+    C = top / (sum(a ** k / math.factorial(k) for k in range(m)) + top)
+    return a + C * rho / (1 - rho)
+
+
+def test_steady_state_bracketing(orc):
+    """Theorem 1: in steady state N^f <= N <= N^b with E[N^b] - E[N^f] = lambda h;
+    E[N] is the Erlang-C mean."""
+    m, mu, lam, h = 5, 1.0, 4.0, 0.2
+    K, R, burn = 12000, 40, 1000
+    run = W.single_station(m, mu, lam, h, K * h, R, 71, N0=7)
+    b = orc.simulate(run.net, 0, h, K * h, R, 71, trace=True)["N"][burn:, 0, :].mean(axis=0)
+    f = orc.simulate(run.net, 1, h, K * h, R, 71, trace=True)["N"][burn:, 0, :].mean(axis=0)
+    EN = _erlang_c_mean(m, lam, mu)
+    gap = b - f
+    se_gap = gap.std() / math.sqrt(R)
+    assert abs(gap.mean() - lam * h) < 5 * se_gap + 0.02
+    assert f.mean() < EN < b.mean()
+    assert abs((b.mean() + f.mean()) / 2 - EN) < 0.2 * EN
+
+
+def test_network_steady_state_gap(orc):
+    """Theorem 2(i): per node E[N^b(i)] - E[N^f(i)] = lambda~_i h (tandem with
+    exits, lambda~ from the traffic equations)."""
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, 0.8)])
+    arr = W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([4.0, 0.0]), a=1.0, b=0.0)
+    net = W.Network(2, row_ptr, col, prob, np.array([5, 4]), np.array([1.25, 1.5]), arr,
+                    N0=np.array([3, 2]))
+    h, K, R, burn = 0.25, 10000, 40, 800
+    b = orc.simulate(net, 0, h, K * h, R, 81, trace=True)["N"][burn:].mean(axis=0)
+    f = orc.simulate(net, 1, h, K * h, R, 81, trace=True)["N"][burn:].mean(axis=0)
+    lam_tot = np.array([4.0, 3.2])
+    for i in range(2):
+        gap = b[i] - f[i]
+        assert abs(gap.mean() - lam_tot[i] * h) < 5 * gap.std() / math.sqrt(R) + 0.02
+
+
+@pytest.mark.parametrize("kind", ["sinusoid", "table"])
+def test_arrival_integral(orc, kind):
+    """Sec. 2.1.1: the step's arrival count is Poisson with mean the integral of
+    lambda over the step; summed over steps it matches the horizon integral."""
+    n = 2
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    if kind == "sinusoid":
+        arr = W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([3.0, 7.0]), a=1.5, b=0.6, period=5.0,
+                         phase=0.7)
+    else:
+        tab = np.array([[1.0, 0.0], [4.0, 2.0], [0.5, 6.0], [2.0, 1.0]])
+        arr = W.Arrivals(kind=W.ARR_TABLE, table=tab, tab_dt=1.3)
+    net = W.Network(n, row_ptr, np.zeros(0), np.zeros(0), np.array([5, 5]), np.array([1.0, 1.0]), arr)
+    dt, T, R = 0.07, 6.0, 5000
+    res = orc.simulate(net, 0, dt, T, R, 91)
+    K = res["K"]
+    Tp = K * dt
+    if kind == "sinusoid":
+        om = 2 * math.pi / arr.period
+        want = arr.w * arr.a * (Tp + arr.b * (math.cos(arr.phase) - math.cos(om * Tp + arr.phase)) / om)
+    else:
+        grid = np.linspace(0.0, Tp, 200001)
+        tpts = np.arange(tab.shape[0]) * arr.tab_dt
+        want = np.array([np.trapezoid(np.interp(grid, tpts, tab[:, i]), grid) for i in range(n)])
+    got = res["station"][:, 4] / R
+    assert np.all(np.abs(got - want) < 5 * np.sqrt(want / R))
+
+
+def test_stats_invariants_and_trace(orc):
+    """Stats equal the sums of the traced trajectories; customers are conserved."""
+    rng = np.random.default_rng(5)
+    net = W.random_small_dag(rng, 9, ext_frac=0.5, lam_scale=8.0)
+    net.N0 = rng.integers(0, 6, size=9).astype(np.int32)
+    dt, T, R = 0.1, 3.0, 64
+    for scheme in (0, 1):
+        res = orc.simulate(net, scheme, dt, T, R, 3, trace=True)
+        N, D, A = res["N"].astype(np.int64), res["D"].astype(np.int64), res["A"].astype(np.int64)
+        st, rp = res["station"], res["rep"]
+        assert np.array_equal(st[:, 0], N.sum(axis=(0, 2)))
+        assert np.array_equal(st[:, 1], np.minimum(N, net.servers[None, :, None]).sum(axis=(0, 2)))
+        assert np.array_equal(st[:, 2], D.sum(axis=(0, 2)))
+        assert np.array_equal(st[:, 4], A.sum(axis=(0, 2)))
+        assert np.array_equal(rp[:, 0], N.sum(axis=(0, 1)))
+        assert np.array_equal(rp[:, 1], D.sum(axis=(0, 1)))
+        assert np.array_equal(res["NK"], N[-1].sum(axis=1))
+        assert st[:, 3].sum() == rp[:, 2].sum() and st[:, 0].sum() == rp[:, 0].sum()
+        total_end = N[-1].sum(axis=0)
+        assert np.array_equal(total_end, net.N0.sum() + rp[:, 3] - rp[:, 2])
+
+
+def test_rep_subsets_are_keyed(orc):
+    """Counter-based keying: a replication's results do not depend on which
+    batch of replications it is run in (rep_begin offsets)."""
+    run = W.tandem3(R=12)
+    full = orc.simulate(run.net, 1, run.dt, 2.0, 12, 9)
+    a = orc.simulate(run.net, 1, run.dt, 2.0, 5, 9, rep_begin=0)
+    b = orc.simulate(run.net, 1, run.dt, 2.0, 7, 9, rep_begin=5)
+    assert np.array_equal(full["rep"], np.concatenate([a["rep"], b["rep"]]))
+    assert np.array_equal(full["station"], a["station"] + b["station"])
+
+
+def test_sampler_cap_error_path(orc):
+    """A rejection loop that hits its cap reports EO_ERR_SAMPLER_CAP (-5)."""
+    run = W.single_station(1000, 1.0, 3000.0, 0.01, 1.0, 50, 1)
+    old = orc.set_cap(1)
+    try:
+        res = orc.simulate(run.net, 0, 0.01, 1.0, 50, 1, expect_ok=False)
+    finally:
+        orc.set_cap(old)
+    assert res["rc"] == -5
+
+
+def test_validation_errors(orc):
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, 0.5), (1, 0, 0.5)])
+    arr = W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([1.0, 0.0]))
+    cyc = W.Network(2, row_ptr, col, prob, np.array([1, 1]), np.array([1.0, 1.0]), arr)
+    assert orc.simulate(cyc, 1, 0.1, 1.0, 2, 1, expect_ok=False)["rc"] == -2
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, 1.5)])
+    bad = W.Network(2, row_ptr, col, prob, np.array([1, 1]), np.array([1.0, 1.0]), arr)
+    assert orc.simulate(bad, 0, 0.1, 1.0, 2, 1, expect_ok=False)["rc"] == -1
