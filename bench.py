@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Throughput of the Euler step on GB300: station-step updates per second.
+
+Workload: the 100-station layered random DAG (10 layers x 10 stations,
+m_i ~ U{100..1000}, mu_i log-uniform on [0.5, 2], utilisation <= 0.9),
+10,000 replications, T = 100, dt = 0.01 (K = 10,000 steps).  One benchmark
+step = one backward-scheme run plus one forward-scheme run over the whole
+workload (2 x 10^10 station-step updates), through the library's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replication range (replication
+indices rank*R ... rank*R+R-1: weak scaling, no data-path collective); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "station-step updates/s per GB300 (fwd/bwd Euler), % of binding roofline"
+UNIT = "station-step updates/s"
+SMS = 152
+LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
+# DRAM bytes per launch of the persistent kernel from ncu (profiles/), valid for
+# the kernel sources with this hash; None when the sources changed since.
+TRAFFIC = {"hash": None, "bytes_per_launch": None}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "sampling.cuh"):
+        with open(os.path.join(ROOT, "paper_2402_13259_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def workload():
+    from paper_2402_13259_gb300 import workloads as W
+    return W.layered_dag()
+
+
+def config_dict(run, K, world):
+    return {
+        "workload": "dag100: 100-station layered random DAG (10x10), R=10000 replications, "
+                    "T=100, dt=0.01 (K=10000 steps), backward + forward scheme per step",
+        "stations": run.net.n, "edges": run.net.nnz, "replications_per_gpu": run.R,
+        "steps_K": K, "schemes": ["backward", "forward"],
+        "state": "int32 station counts, int64 statistics, float32 samplers",
+        "l2": "flushed between steps (256 MiB write)",
+        "parallelism": f"replication ranges, {world} rank(s)",
+    }
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(run, K_full, reps=12):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same workload: `reps` replications x the full horizon, both schemes."""
+    from oracle import oracle as O
+    from paper_2402_13259_gb300 import opmodel
+    per_scheme = {}
+    total_units, total_t = 0, 0.0
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        O.counters_reset()
+        t0 = time.perf_counter()
+        O.simulate(run.net, scheme, run.dt, run.T, reps, run.seed, rep_begin=0)
+        dt = time.perf_counter() - t0
+        c = O.counters()
+        units = run.net.n * K_full * reps
+        per_scheme[name] = {"ops_per_unit": opmodel.ops_per_unit(c),
+                            "philox_blocks_per_unit": c["philox_blocks"] / max(c["units"], 1)}
+        total_units += units
+        total_t += dt
+    return {"value": total_units / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} replications x {K_full} steps x {run.net.n} stations, both schemes "
+                      f"(single-threaded C oracle)", "seconds": total_t}, per_scheme
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    run = workload()
+    K = O.num_steps(run.dt, run.T)
+    reps = 2
+    units_per_step = 2 * run.net.n * K * reps
+    for _ in range(args.warmup):
+        for scheme in (0, 1):
+            O.simulate(run.net, scheme, run.dt, run.T, reps, run.seed)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for scheme in (0, 1):
+            O.simulate(run.net, scheme, run.dt, run.T, reps, run.seed, rep_begin=reps * k)
+    el = time.perf_counter() - t0
+    value = units_per_step * args.steps / el
+    cfg = config_dict(run, K, 1)
+    cfg["replications_per_step"] = reps
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{reps} replications x {K} steps x {run.net.n} stations "
+                                       "per scheme per step, single-threaded C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2402_13259_gb300 import binding as Bd
+    run = workload()
+    K = Bd.num_steps(run.dt, run.T)
+    n, R = run.net.n, run.R
+    rep_begin = rank * R
+    units_per_step = 2 * n * K * R  # per rank
+    h = Bd.EulerNet(run.net)
+    stream = torch.cuda.current_stream()
+    stats = [torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda") for _ in range(2)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+
+    def one_step(events=None):
+        flush.fill_(1)
+        for scheme in (0, 1):
+            if events is not None:
+                events[scheme][0].record(stream)
+            h.simulate(scheme, run.dt, run.T, R, run.seed, rep_begin, stats=stats[scheme], check=False)
+            if events is not None:
+                events[scheme][1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    h.status()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        one_step(ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    h.status()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kern_ms = [sum(ev[k][s][0].elapsed_time(ev[k][s][1]) for k in range(args.steps)) / args.steps
+               for s in (0, 1)]
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * units_per_step / (ms_per_step / 1e3)
+
+    # end to end through the host-buffer entry point: network upload, both
+    # schemes, statistics copied back to host memory, every step
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        out = [np.empty(Bd.stats_len(n, R), dtype=np.int64) for _ in range(2)]
+        torch.cuda.synchronize()
+        h2d = 0
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            he = Bd.EulerNet(run.net)
+            for scheme in (0, 1):
+                he.simulate_host(scheme, run.dt, run.T, R, run.seed, rep_begin, out=out[scheme])
+            h2d = he.h2d_bytes()
+            he.close()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 2 * 8 * Bd.stats_len(n, R)}
+    h.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    base, per_scheme = (None, None)
+    if not args.no_cpu_baseline:
+        base, per_scheme = cpu_baseline(run, K)
+    units_launch = n * K * R
+    roof = None
+    if per_scheme:
+        ops = [per_scheme["backward"]["ops_per_unit"] * units_launch,
+               per_scheme["forward"]["ops_per_unit"] * units_launch]
+        achieved = sum(ops) / (sum(kern_ms) / 1e3)
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak = SMS * LANES_PER_SM * sm_max * 1e6
+        valid = TRAFFIC["hash"] == kernel_hash()
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak,
+                "traffic": TRAFFIC["bytes_per_launch"] if valid else None,
+                "kernel": "persistent_kernel", "ops_per_unit": {k: v["ops_per_unit"] for k, v in per_scheme.items()},
+                "peak_note": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz (issue rate)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(run, K, world),
+        "per_scheme": {"backward": {"ms_per_launch": kern_ms[0], "value": units_launch / (kern_ms[0] / 1e3)},
+                       "forward": {"ms_per_launch": kern_ms[1], "value": units_launch / (kern_ms[1] / 1e3)}},
+        "roofline": roof, "cpu_baseline": base, "e2e": e2e, "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "plan": {"backward": Bd.EulerNet(run.net).plan(0, R), "forward": Bd.EulerNet(run.net).plan(1, R)},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * eulernet.h -- C ABI of the GB300 (sm_103a) Euler-approximation simulator
+ * for feedforward Markovian queueing networks.
+ *
+ * Method: Hong, Song & Wang, "Fast Discrete-Event Simulation of Markovian
+ * Queueing Networks through Euler Approximation" (arXiv 2402.13259).
+ *   - one Euler step of a network, backward scheme: Sec. 2.2 (task list 1-4),
+ *     Algorithm 2;
+ *   - one Euler step, forward scheme: Sec. 2.2 (task list 1-4), Algorithm 3,
+ *     taken node by node in flow order for a feedforward network;
+ *   - external arrivals per step: Sec. 2.1.1 (Poisson count with mean the
+ *     integral of lambda_i over the step);
+ *   - departures per step: GenerateDeparture, Lemma 1 / Algorithm 1;
+ *   - routing: the multinomial split of Sec. 2.2.
+ *
+ * Conventions.
+ *   - Every function returns EULER_OK (0) or a negative EULER_ERR_* code and
+ *     never aborts; euler_net_last_error() returns a thread-local message for
+ *     the last failure on the calling thread.
+ *   - Host pointers are read during the call only and never retained.
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     results are written asynchronously on the given stream (a cudaStream_t
+ *     passed as void*, NULL = the legacy default stream).
+ *   - Randomness: Philox4x32-10 keyed by (seed; replication, step, station,
+ *     purpose).  A replication's results do not depend on the launch shape,
+ *     on the tile it ran in or on which other replications ran with it.
+ */
+#ifndef EULERNET_H
+#define EULERNET_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EULERNET_API __attribute__((visibility("default")))
+#else
+#define EULERNET_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  EULER_OK = 0,
+  EULER_ERR_ARG = -1,             /* invalid argument (reported synchronously)    */
+  EULER_ERR_NOT_FEEDFORWARD = -2, /* routing graph has a cycle                    */
+  EULER_ERR_CUDA = -3,            /* a CUDA runtime call failed                   */
+  EULER_ERR_OOM = -4,             /* device allocation failed                     */
+  EULER_ERR_SAMPLER_CAP = -5,     /* a rejection loop hit its iteration cap       */
+  EULER_ERR_OVERFLOW = -6,        /* a station count exceeded 2^30                */
+  EULER_ERR_TOO_LARGE = -7        /* sizes beyond this library's index ranges     */
+};
+
+enum { EULER_BACKWARD = 0, EULER_FORWARD = 1 };
+enum { EULER_ARR_NONE = 0, EULER_ARR_SINUSOID = 1, EULER_ARR_TABLE = 2 };
+
+/* External arrival rate lambda_i(t) (Sec. 2.2, "customers arriving at the
+ * i-th node from outside ... Poisson process with rate lambda_i", allowed to
+ * vary in time, Sec. 2.1).
+ *   EULER_ARR_SINUSOID: lambda_i(t) = w[i] * a * (1 + b sin(2 pi t / period + phase))
+ *   EULER_ARR_TABLE:    piecewise linear through (j * tab_dt, table[j*n + i]),
+ *                       j = 0..table_len-1, held constant after the last point.
+ * The per-step mean is the exact integral of lambda_i over the step,
+ * computed in double on the host. */
+typedef struct {
+  int32_t kind;
+  const double* w;  /* [n] (sinusoid)                  */
+  double a, b, period, phase;
+  const double* table; /* [table_len][n] (table)       */
+  int32_t table_len;
+  double tab_dt;
+} euler_arrivals;
+
+typedef struct euler_net euler_net; /* opaque; owns device copies of the tables */
+
+/* Build a network (host only, plus a one-time upload of immutable tables to
+ * the current device).
+ *   n        number of stations, 1 <= n < 2^24
+ *   row_ptr  [n+1] CSR offsets of the routing matrix P (row i = station i)
+ *   col      [nnz] destination station of each edge (no self loops)
+ *   prob     [nnz] p_ij in [0,1]; exit probability p_i_exit = 1 - row sum,
+ *            row sums may not exceed 1 + 1e-12
+ *   servers  [n] m_i >= 1 (constant in time)
+ *   mu       [n] service rate per server, finite and > 0
+ *   arrivals external arrival rates (may be NULL: no external arrivals)
+ *   N0       [n] initial customers per station, or NULL for an empty network
+ * The graph must be feedforward (acyclic); stations are grouped into levels
+ * (longest path from a source) for the forward scheme.
+ * Errors: EULER_ERR_ARG, EULER_ERR_NOT_FEEDFORWARD, EULER_ERR_OOM,
+ * EULER_ERR_CUDA.  On error *out is set to NULL. */
+EULERNET_API int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const int32_t* col,
+                     const double* prob, const int32_t* servers, const double* mu,
+                     const euler_arrivals* arrivals, const int32_t* N0);
+
+/* Number of int64 entries of the stats buffer for n stations and R
+ * replications: 6n + 4R. */
+EULERNET_API int64_t euler_stats_len(int32_t n, int64_t replications);
+
+/* Simulate `replications` independent replications of the backward
+ * (Algorithm 2) or forward (Algorithm 3) scheme with step dt over
+ * K = ceil(T/dt - 1e-9) steps, replication indices rep_begin ..
+ * rep_begin + replications - 1 (the index keys the random streams, so a
+ * range can be split across calls or devices and give identical results).
+ *
+ * stats: caller-owned DEVICE buffer of euler_stats_len(n, R) int64, fully
+ * overwritten, with the sums over steps tau = 1..K of post-update values:
+ *   [n][5]  per station  {Q_i = sum N, B_i = sum min(N, m_i), D_i = sum D,
+ *                         X_i = sum exits, A_i = sum external arrivals}
+ *   [R][4]  per replication {Q_r, D_r, X_r, A_r} (also summed over stations)
+ *   [n]     N_K summed over replications.
+ *
+ * Asynchronous on cuda_stream.  Argument errors are returned synchronously;
+ * device-side errors (EULER_ERR_SAMPLER_CAP, EULER_ERR_OVERFLOW) are latched
+ * in the handle and returned by euler_net_status().  Calls on one handle must
+ * not overlap on different streams (the handle's per-call tables and error
+ * word are shared).  The handle caches the per-dt tables of its last call. */
+EULERNET_API int euler_net_simulate(euler_net* net, int32_t scheme, double dt, double T,
+                       int64_t replications, uint64_t seed, int64_t rep_begin,
+                       int64_t* stats, void* cuda_stream);
+
+/* Same as euler_net_simulate with HOST input and output: copies nothing in
+ * (the network already lives on the device), allocates a temporary device
+ * stats buffer, runs, copies the stats back into host memory `stats_host`
+ * and synchronises.  Returns the device-side status as well. */
+EULERNET_API int euler_net_simulate_host(euler_net* net, int32_t scheme, double dt, double T,
+                            int64_t replications, uint64_t seed, int64_t rep_begin,
+                            int64_t* stats_host, void* cuda_stream);
+
+/* Synchronise `cuda_stream`, then return and clear the latched device-side
+ * status of the handle's previous calls (EULER_OK if none failed). */
+EULERNET_API int euler_net_status(euler_net* net, void* cuda_stream);
+
+/* Tuning and testing options (see EULER_OPT_*); value < 0 restores the
+ * default.  Returns EULER_OK or EULER_ERR_ARG. */
+enum {
+  EULER_OPT_FORM = 0,        /* 0 = auto, 1 = persistent shared-memory kernel,
+                                2 = per-step kernels over HBM state (graph)    */
+  EULER_OPT_TILE_REPS = 1,   /* replications per tile (power of two)           */
+  EULER_OPT_BLOCK = 2,       /* threads per block                              */
+  EULER_OPT_GRID = 3,        /* blocks of the persistent kernel (0 = auto)     */
+  EULER_OPT_SAMPLER_CAP = 4, /* rejection-loop iteration cap (default 1000)    */
+  EULER_OPT_GRAPH_STEPS = 5  /* steps captured per CUDA graph (HBM form)       */
+};
+EULERNET_API int euler_net_set_option(euler_net* net, int32_t option, int64_t value);
+
+/* Describe the launch the next euler_net_simulate would make for these
+ * sizes: form (1 or 2), tile replications, block, grid, shared bytes.
+ * Host only; no device work. */
+EULERNET_API int euler_net_plan(euler_net* net, int32_t scheme, int64_t replications, int32_t* form,
+                   int32_t* tile_reps, int32_t* block, int32_t* grid, int32_t* smem_bytes);
+
+/* Host-to-device bytes this handle has copied so far (network tables at
+ * creation plus the per-(dt, T) step tables), or -1 for a NULL handle. */
+EULERNET_API int64_t euler_net_h2d_bytes(const euler_net* net);
+
+/* Number of Euler steps used for (dt, T): ceil(T/dt - 1e-9), at least 1. */
+EULERNET_API int64_t euler_num_steps(double dt, double T);
+
+EULERNET_API void euler_net_destroy(euler_net* net);
+EULERNET_API const char* euler_net_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EULERNET_H */

@@ -1,0 +1,186 @@
+"""Thin ctypes binding of ``libeulernet.so`` (argument marshalling only).
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+only converts a :class:`workloads.Network` into the C ABI's arrays, hands
+torch-allocated device buffers and the current torch stream to the library,
+and maps error codes to exceptions.  There is no CPU fallback: if the library
+is missing the import-time loader raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+from .workloads import Network
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeulernet.so")
+
+BACKWARD, FORWARD = 0, 1
+OPT_FORM, OPT_TILE_REPS, OPT_BLOCK, OPT_GRID, OPT_SAMPLER_CAP, OPT_GRAPH_STEPS = range(6)
+
+ERRORS = {
+    -1: "EULER_ERR_ARG", -2: "EULER_ERR_NOT_FEEDFORWARD", -3: "EULER_ERR_CUDA", -4: "EULER_ERR_OOM",
+    -5: "EULER_ERR_SAMPLER_CAP", -6: "EULER_ERR_OVERFLOW", -7: "EULER_ERR_TOO_LARGE",
+}
+
+
+class EulerError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Arrivals(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("w", C.c_void_p), ("a", C.c_double), ("b", C.c_double),
+                ("period", C.c_double), ("phase", C.c_double), ("table", C.c_void_p),
+                ("table_len", C.c_int32), ("tab_dt", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        L.euler_net_create.argtypes = [C.POINTER(vp), i32, vp, vp, vp, vp, vp, C.POINTER(_Arrivals), vp]
+        L.euler_net_create.restype = C.c_int
+        L.euler_net_simulate.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp]
+        L.euler_net_simulate.restype = C.c_int
+        L.euler_net_simulate_host.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp]
+        L.euler_net_simulate_host.restype = C.c_int
+        L.euler_net_status.argtypes = [vp, vp]
+        L.euler_net_status.restype = C.c_int
+        L.euler_net_set_option.argtypes = [vp, i32, i64]
+        L.euler_net_set_option.restype = C.c_int
+        L.euler_net_plan.argtypes = [vp, i32, i64] + [C.POINTER(i32)] * 5
+        L.euler_net_plan.restype = C.c_int
+        L.euler_stats_len.argtypes = [i32, i64]
+        L.euler_stats_len.restype = i64
+        L.euler_num_steps.argtypes = [dbl, dbl]
+        L.euler_num_steps.restype = i64
+        L.euler_net_h2d_bytes.argtypes = [vp]
+        L.euler_net_h2d_bytes.restype = i64
+        L.euler_net_destroy.argtypes = [vp]
+        L.euler_net_destroy.restype = None
+        L.euler_net_last_error.argtypes = []
+        L.euler_net_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise EulerError(rc, lib().euler_net_last_error().decode())
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def num_steps(dt: float, T: float) -> int:
+    return int(lib().euler_num_steps(dt, T))
+
+
+def stats_len(n: int, R: int) -> int:
+    return int(lib().euler_stats_len(n, R))
+
+
+def split_stats(stats, n: int, R: int) -> Dict[str, object]:
+    """Views of a flat stats buffer (numpy array or torch tensor)."""
+    return {"station": stats[: 5 * n].reshape(n, 5),
+            "rep": stats[5 * n: 5 * n + 4 * R].reshape(R, 4),
+            "NK": stats[5 * n + 4 * R: 6 * n + 4 * R]}
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class EulerNet:
+    """A network resident on the current CUDA device."""
+
+    def __init__(self, net: Network):
+        L = lib()
+        self.n = net.n
+        a = net.arrivals
+        arr = _Arrivals()
+        arr.kind = a.kind
+        keep = [net.row_ptr, net.col, net.prob, net.servers, net.mu]
+        if a.w is not None:
+            arr.w = _ptr(a.w)
+            keep.append(a.w)
+        arr.a, arr.b, arr.period, arr.phase = a.a, a.b, a.period, a.phase
+        if a.table is not None:
+            arr.table = _ptr(a.table)
+            arr.table_len = a.table.shape[0]
+            keep.append(a.table)
+        arr.tab_dt = a.tab_dt
+        h = C.c_void_p()
+        rc = L.euler_net_create(C.byref(h), net.n, _ptr(net.row_ptr),
+                                _ptr(net.col) if net.nnz else None,
+                                _ptr(net.prob) if net.nnz else None, _ptr(net.servers), _ptr(net.mu),
+                                C.byref(arr), _ptr(net.N0))
+        del keep
+        _check(rc)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().euler_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def h2d_bytes(self) -> int:
+        return int(lib().euler_net_h2d_bytes(self._h))
+
+    def set_option(self, option: int, value: int):
+        _check(lib().euler_net_set_option(self._h, option, value))
+
+    def plan(self, scheme: int, R: int) -> Dict[str, int]:
+        vals = [C.c_int32() for _ in range(5)]
+        _check(lib().euler_net_plan(self._h, scheme, R, *[C.byref(v) for v in vals]))
+        return dict(zip(["form", "tile_reps", "block", "grid", "smem"], (v.value for v in vals)))
+
+    def simulate(self, scheme: int, dt: float, T: float, R: int, seed: int, rep_begin: int = 0,
+                 stats=None, stream=None, check: bool = True):
+        """Run on the device; returns the int64 stats tensor (device).  With
+        check=True the stream is synchronised and device-side errors raise."""
+        import torch
+        n = self.n
+        if stats is None:
+            stats = torch.empty(stats_len(n, R), dtype=torch.int64, device="cuda")
+        sp = _stream_ptr(stream)
+        _check(lib().euler_net_simulate(self._h, scheme, dt, T, R, seed, rep_begin,
+                                        C.c_void_p(stats.data_ptr()), C.c_void_p(sp)))
+        if check:
+            self.status(stream)
+        return stats
+
+    def status(self, stream=None):
+        _check(lib().euler_net_status(self._h, C.c_void_p(_stream_ptr(stream))))
+
+    def simulate_host(self, scheme: int, dt: float, T: float, R: int, seed: int,
+                      rep_begin: int = 0, out: Optional[np.ndarray] = None, stream=None) -> np.ndarray:
+        """Run with a host-memory result buffer (the library copies it back)."""
+        if out is None:
+            out = np.empty(stats_len(self.n, R), dtype=np.int64)
+        _check(lib().euler_net_simulate_host(self._h, scheme, dt, T, R, seed, rep_begin, _ptr(out),
+                                             C.c_void_p(_stream_ptr(stream))))
+        return out

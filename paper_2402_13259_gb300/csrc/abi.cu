@@ -1,0 +1,599 @@
+// abi.cu -- host side of the C ABI declared in include/eulernet.h.
+//
+// euler_net_create validates the network (Sec. 2.2: routing probabilities
+// p_ij with exit probability 1 - sum_j p_ij, servers m_i, rates mu_i), orders
+// stations into levels by longest path (the flow order the forward scheme of
+// Algorithm 3 needs for a feedforward network), builds the reverse graph for
+// the gather of internal arrivals (Sec. 2.2, A^in_i = sum_k R_ki) and the
+// conditional split probabilities of the sequential-binomial multinomial, and
+// uploads everything once.  euler_net_simulate computes the per-step arrival
+// means (Sec. 2.1.1, the integral of lambda_i over each step) for its (dt, T),
+// picks the launch form and runs it asynchronously.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/eulernet.h"
+#include "internal.h"
+#include "sampling.cuh"
+
+using namespace eulernet;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? EULER_ERR_OOM : EULER_ERR_CUDA;
+}
+
+#define CUDA_TRY(expr)                              \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src, int64_t* counter) {
+  *dst = nullptr;
+  *counter += (int64_t)(src.size() * sizeof(T));
+  const size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+}  // namespace
+
+struct euler_net {
+  int32_t n = 0, E = 0, L = 0, max_level = 0, n_ex = 0;
+  std::vector<int32_t> row_ptr, col, servers, lvl_ptr, lvl_station, ex_col, N0;
+  std::vector<double> prob, mu;
+  int32_t arr_kind = EULER_ARR_NONE;
+  std::vector<double> w, table;
+  double a = 0, b = 0, period = 1, phase = 0, tab_dt = 1;
+  int32_t table_len = 0;
+
+  int device = 0, sm_count = 0, smem_optin = 0;
+  int32_t *d_lvl_ptr = nullptr, *d_lvl_station = nullptr, *d_row_ptr = nullptr, *d_in_ptr = nullptr,
+          *d_in_edge = nullptr, *d_servers = nullptr, *d_N0 = nullptr, *d_ex_col = nullptr;
+  float *d_qc = nullptr, *d_mu = nullptr;
+  unsigned* d_err = nullptr;
+
+  // per-(dt, T) tables of the last call
+  double c_dt = -1.0, c_T = -1.0;
+  int32_t c_K = 0;
+  float* d_p0 = nullptr;
+  float* d_lam = nullptr;
+  size_t lam_cap = 0;
+
+  // HBM-form state
+  int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr;
+  int64_t* d_racc = nullptr;
+  int64_t hbm_cap_ld = 0, hbm_cap_R = 0;
+  cudaStream_t cap_stream = nullptr;
+
+  int64_t opt[6] = {-1, -1, -1, -1, -1, -1};
+  int64_t h2d_bytes = 0;  // host-to-device bytes copied by this handle so far
+
+  NetTables tables() const {
+    NetTables t;
+    t.n = n;
+    t.E = E;
+    t.L = L;
+    t.max_level = max_level;
+    t.lvl_ptr = d_lvl_ptr;
+    t.lvl_station = d_lvl_station;
+    t.row_ptr = d_row_ptr;
+    t.qc = d_qc;
+    t.in_ptr = d_in_ptr;
+    t.in_edge = d_in_edge;
+    t.servers = d_servers;
+    t.mu = d_mu;
+    t.N0 = N0.empty() ? nullptr : d_N0;
+    t.ex_col = d_ex_col;
+    t.n_ex = n_ex;
+    return t;
+  }
+};
+
+namespace {
+
+// Per-step mean of the external arrivals: the exact integral of lambda_i over
+// ((tau-1) dt, tau dt] (Sec. 2.1.1), in double.
+double step_mean(const euler_net& h, int32_t i, int64_t tau, double dt) {
+  const double t0 = (double)(tau - 1) * dt;
+  const double t1 = (double)tau * dt;
+  if (h.arr_kind == EULER_ARR_SINUSOID) {
+    const double om = 6.283185307179586 / h.period;
+    const double lam =
+        h.w[i] * h.a * ((t1 - t0) + h.b * (cos(om * t0 + h.phase) - cos(om * t1 + h.phase)) / om);
+    return lam > 0.0 ? lam : 0.0;
+  }
+  if (h.arr_kind == EULER_ARR_TABLE) {
+    const int32_t J = h.table_len, n = h.n;
+    const double td = h.tab_dt;
+    double total = 0.0;
+    double a = t0;
+    while (a < t1) {
+      const int64_t j = (int64_t)floor(a / td);
+      const double seg_end = (double)(j + 1) * td;
+      double b = seg_end < t1 ? seg_end : t1;
+      if (b <= a) b = t1;
+      double la, lb;
+      if (j >= J - 1) {
+        la = lb = h.table[(int64_t)(J - 1) * n + i];
+      } else {
+        const double y0 = h.table[j * n + i], y1 = h.table[(j + 1) * n + i];
+        const double ta = (double)j * td;
+        la = y0 + (y1 - y0) * ((a - ta) / td);
+        lb = y0 + (y1 - y0) * ((b - ta) / td);
+      }
+      total += (b - a) * (la + lb) * 0.5;
+      a = b;
+    }
+    return total > 0.0 ? total : 0.0;
+  }
+  return 0.0;
+}
+
+int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
+  const int64_t K = euler_num_steps(dt, T);
+  if (h->c_dt == dt && h->c_T == T) return EULER_OK;
+  std::vector<float> p0(h->n);
+  for (int32_t i = 0; i < h->n; ++i) {
+    const float y = (float)(h->mu[i] * dt);
+    p0[i] = -fm::expm1(-y);
+  }
+  std::vector<float> lam((size_t)K * std::max(h->n_ex, 1), 0.0f);
+  for (int32_t i = 0; i < h->n; ++i) {
+    const int32_t c = h->ex_col[i];
+    if (c < 0) continue;
+    for (int64_t tau = 1; tau <= K; ++tau) lam[(size_t)(tau - 1) * h->n_ex + c] = (float)step_mean(*h, i, tau, dt);
+  }
+  if (!h->d_p0) CUDA_TRY(cudaMalloc(&h->d_p0, sizeof(float) * (size_t)h->n));
+  if (lam.size() > h->lam_cap) {
+    if (h->d_lam) CUDA_TRY(cudaFree(h->d_lam));
+    h->d_lam = nullptr;
+    CUDA_TRY(cudaMalloc(&h->d_lam, sizeof(float) * lam.size()));
+    h->lam_cap = lam.size();
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_p0, p0.data(), sizeof(float) * p0.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(h->d_lam, lam.data(), sizeof(float) * lam.size(), cudaMemcpyHostToDevice, s));
+  h->h2d_bytes += (int64_t)(sizeof(float) * (p0.size() + lam.size()));
+  CUDA_TRY(cudaStreamSynchronize(s));  // host staging buffers go out of scope
+  h->c_dt = dt;
+  h->c_T = T;
+  h->c_K = (int32_t)K;
+  return EULER_OK;
+}
+
+struct Plan {
+  int form = 1, tile_reps = 32, block = 32, grid = 1;
+  int64_t smem = 0, num_tiles = 0;
+};
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
+  const int64_t limit = h->smem_optin;
+  const int forced_form = (int)h->opt[EULER_OPT_FORM];
+  int Rt = -1;
+  if (h->opt[EULER_OPT_TILE_REPS] > 0) {
+    Rt = (int)h->opt[EULER_OPT_TILE_REPS];
+    if (!is_pow2(Rt) || Rt > 512) return fail(EULER_ERR_ARG, "tile replications must be a power of two <= 512");
+  } else {
+    for (int cand = 32; cand >= 1; cand >>= 1)
+      if (persistent_smem_bytes(h->n, h->E, cand) <= limit) {
+        Rt = cand;
+        break;
+      }
+  }
+  pl->form = (forced_form == 1 || forced_form == 2) ? forced_form : 1;
+  if (pl->form == 1 && (Rt < 1 || persistent_smem_bytes(h->n, h->E, Rt) > limit)) {
+    if (forced_form == 1) return fail(EULER_ERR_TOO_LARGE, "network tile does not fit in shared memory");
+    pl->form = 2;
+  }
+  if (pl->form == 2) {
+    pl->tile_reps = 32;
+    pl->block = h->opt[EULER_OPT_BLOCK] > 0 ? (int)h->opt[EULER_OPT_BLOCK] : 256;
+    if (pl->block % 32 || pl->block > 256) return fail(EULER_ERR_ARG, "HBM-form block must be a multiple of 32 <= 256");
+    pl->grid = 0;
+    pl->smem = 0;
+    pl->num_tiles = (R + 31) / 32;
+    return EULER_OK;
+  }
+  pl->tile_reps = Rt;
+  const int64_t m_max = scheme == EULER_BACKWARD ? h->n : h->max_level;
+  const int quantum = Rt >= 32 ? 1 : 32 / Rt;  // groups per warp
+  int block;
+  if (h->opt[EULER_OPT_BLOCK] > 0) {
+    block = (int)h->opt[EULER_OPT_BLOCK];
+    if (block % 32 || block % Rt || block > 512) return fail(EULER_ERR_ARG, "block must be a multiple of 32 and of the tile, <= 512");
+  } else {
+    const int64_t gmax = std::max<int64_t>(512 / Rt, 1);
+    const int64_t iters = (m_max + gmax - 1) / gmax;
+    int64_t G = (m_max + iters - 1) / iters;
+    G = (G + quantum - 1) / quantum * quantum;
+    if (G * Rt > 512) G = 512 / Rt;
+    block = (int)std::max<int64_t>(G * Rt, 32);
+  }
+  pl->block = block;
+  pl->smem = persistent_smem_bytes(h->n, h->E, Rt);
+  pl->num_tiles = (R + Rt - 1) / Rt;
+  int per_sm = 0;
+  cudaError_t e = persistent_occupancy(block, (int)pl->smem, &per_sm);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (per_sm < 1) {
+    if (forced_form == 1) return fail(EULER_ERR_TOO_LARGE, "persistent kernel cannot be resident");
+    pl->form = 2;
+    pl->tile_reps = 32;
+    pl->block = 256;
+    pl->num_tiles = (R + 31) / 32;
+    return EULER_OK;
+  }
+  int64_t grid = (int64_t)per_sm * h->sm_count;
+  if (h->opt[EULER_OPT_GRID] > 0) grid = h->opt[EULER_OPT_GRID];
+  pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, pl->num_tiles));
+  return EULER_OK;
+}
+
+int ensure_hbm_state(euler_net* h, int64_t R) {
+  const int64_t ld = (R + 3) / 4 * 4;
+  if (ld <= h->hbm_cap_ld && R <= h->hbm_cap_R && h->d_N) return EULER_OK;
+  cudaFree(h->d_N);
+  cudaFree(h->d_Redge);
+  cudaFree(h->d_racc);
+  h->d_N = nullptr;
+  h->d_Redge = nullptr;
+  h->d_racc = nullptr;
+  CUDA_TRY(cudaMalloc(&h->d_N, sizeof(int32_t) * (size_t)h->n * ld));
+  CUDA_TRY(cudaMalloc(&h->d_Redge, sizeof(int32_t) * (size_t)std::max(h->E, 1) * ld));
+  CUDA_TRY(cudaMalloc(&h->d_racc, sizeof(int64_t) * 4 * (size_t)std::max<int64_t>(R, 1)));
+  if (!h->d_tau) CUDA_TRY(cudaMalloc(&h->d_tau, sizeof(int32_t)));
+  h->hbm_cap_ld = ld;
+  h->hbm_cap_R = R;
+  return EULER_OK;
+}
+
+int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl, cudaStream_t s) {
+  int rc = ensure_hbm_state(h, p.R);
+  if (rc) return rc;
+  HbmState hs;
+  hs.N = h->d_N;
+  hs.Redge = h->d_Redge;
+  hs.racc = h->d_racc;
+  hs.tau = h->d_tau;
+  hs.ld = h->hbm_cap_ld;
+  CUDA_TRY(launch_hbm_init(t, p, hs, s));
+  const int64_t S = h->opt[EULER_OPT_GRAPH_STEPS] > 0 ? h->opt[EULER_OPT_GRAPH_STEPS]
+                                                      : std::min<int64_t>(p.K, 32);
+  if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int64_t k = 0; k < S; ++k) {
+    cudaError_t e = launch_hbm_step(t, p, hs, pl.block, h->lvl_ptr.data(), h->cap_stream);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(h->cap_stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(e, "hbm step capture");
+    }
+  }
+  CUDA_TRY(cudaStreamEndCapture(h->cap_stream, &graph));
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  const int64_t replays = (p.K + S - 1) / S;
+  for (int64_t k = 0; k < replays && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  CUDA_TRY(launch_hbm_finish(t, p, hs, s));
+  return EULER_OK;
+}
+
+int validate_net(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* prob,
+                 const int32_t* servers, const double* mu, const euler_arrivals* arr,
+                 const int32_t* N0) {
+  if (n <= 0 || n >= (1 << 24)) return fail(EULER_ERR_ARG, "n must be in [1, 2^24)");
+  if (!row_ptr || !servers || !mu) return fail(EULER_ERR_ARG, "row_ptr, servers and mu are required");
+  if (row_ptr[0] != 0) return fail(EULER_ERR_ARG, "row_ptr[0] must be 0");
+  for (int32_t i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(EULER_ERR_ARG, "row_ptr must be non-decreasing");
+    if (row_ptr[i + 1] >= (1 << 30)) return fail(EULER_ERR_TOO_LARGE, "too many edges");
+    if (servers[i] < 1) return fail(EULER_ERR_ARG, "servers must be >= 1");
+    if (!(mu[i] > 0.0) || !std::isfinite(mu[i])) return fail(EULER_ERR_ARG, "mu must be finite and > 0");
+    if (N0 && (N0[i] < 0 || N0[i] > kStateLimit)) return fail(EULER_ERR_ARG, "N0 out of range");
+  }
+  const int32_t E = row_ptr[n];
+  if (E > 0 && (!col || !prob)) return fail(EULER_ERR_ARG, "col and prob are required");
+  for (int32_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      if (col[e] < 0 || col[e] >= n) return fail(EULER_ERR_ARG, "edge destination out of range");
+      if (col[e] == i) return fail(EULER_ERR_NOT_FEEDFORWARD, "self loop");
+      if (!(prob[e] >= 0.0 && prob[e] <= 1.0)) return fail(EULER_ERR_ARG, "edge probability outside [0,1]");
+      s += prob[e];
+    }
+    if (s > 1.0 + 1e-12) return fail(EULER_ERR_ARG, "routing row sum exceeds 1");
+  }
+  if (arr && arr->kind == EULER_ARR_SINUSOID) {
+    if (!arr->w || !(arr->period > 0.0) || !std::isfinite(arr->a) || !std::isfinite(arr->b))
+      return fail(EULER_ERR_ARG, "bad sinusoid arrival parameters");
+    for (int32_t i = 0; i < n; ++i)
+      if (!(arr->w[i] >= 0.0) || !std::isfinite(arr->w[i])) return fail(EULER_ERR_ARG, "arrival weights must be finite and >= 0");
+  } else if (arr && arr->kind == EULER_ARR_TABLE) {
+    if (!arr->table || arr->table_len < 1 || !(arr->tab_dt > 0.0)) return fail(EULER_ERR_ARG, "bad arrival table");
+    for (int64_t k = 0; k < (int64_t)arr->table_len * n; ++k)
+      if (!(arr->table[k] >= 0.0) || !std::isfinite(arr->table[k])) return fail(EULER_ERR_ARG, "arrival table must be finite and >= 0");
+  } else if (arr && arr->kind != EULER_ARR_NONE) {
+    return fail(EULER_ERR_ARG, "unknown arrival kind");
+  }
+  return EULER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t euler_num_steps(double dt, double T) {
+  const double k = ceil(T / dt - 1e-9);
+  return k < 1.0 ? 1 : (int64_t)k;
+}
+
+int64_t euler_stats_len(int32_t n, int64_t replications) { return 6 * (int64_t)n + 4 * replications; }
+
+const char* euler_net_last_error(void) { return g_last_error.c_str(); }
+
+void euler_net_destroy(euler_net* h) {
+  if (!h) return;
+  cudaFree(h->d_lvl_ptr);
+  cudaFree(h->d_lvl_station);
+  cudaFree(h->d_row_ptr);
+  cudaFree(h->d_in_ptr);
+  cudaFree(h->d_in_edge);
+  cudaFree(h->d_servers);
+  cudaFree(h->d_N0);
+  cudaFree(h->d_ex_col);
+  cudaFree(h->d_qc);
+  cudaFree(h->d_mu);
+  cudaFree(h->d_err);
+  cudaFree(h->d_p0);
+  cudaFree(h->d_lam);
+  cudaFree(h->d_N);
+  cudaFree(h->d_Redge);
+  cudaFree(h->d_racc);
+  cudaFree(h->d_tau);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const int32_t* col,
+                     const double* prob, const int32_t* servers, const double* mu,
+                     const euler_arrivals* arrivals, const int32_t* N0) {
+  if (!out) return fail(EULER_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate_net(n, row_ptr, col, prob, servers, mu, arrivals, N0);
+  if (rc) return rc;
+  euler_net* h = new euler_net();
+  h->n = n;
+  h->E = row_ptr[n];
+  h->row_ptr.assign(row_ptr, row_ptr + n + 1);
+  h->col.assign(col ? col : row_ptr, col ? col + h->E : row_ptr);
+  h->prob.assign(prob ? prob : mu, prob ? prob + h->E : mu);
+  h->servers.assign(servers, servers + n);
+  h->mu.assign(mu, mu + n);
+  if (N0) h->N0.assign(N0, N0 + n);
+  if (arrivals) {
+    h->arr_kind = arrivals->kind;
+    if (arrivals->kind == EULER_ARR_SINUSOID) {
+      h->w.assign(arrivals->w, arrivals->w + n);
+      h->a = arrivals->a;
+      h->b = arrivals->b;
+      h->period = arrivals->period;
+      h->phase = arrivals->phase;
+    } else if (arrivals->kind == EULER_ARR_TABLE) {
+      h->table.assign(arrivals->table, arrivals->table + (int64_t)arrivals->table_len * n);
+      h->table_len = arrivals->table_len;
+      h->tab_dt = arrivals->tab_dt;
+    }
+  }
+
+  // levels by longest path, via Kahn's order; a leftover station means a cycle
+  std::vector<int32_t> indeg(n, 0), level(n, 0), ready;
+  for (int32_t e = 0; e < h->E; ++e) indeg[h->col[e]]++;
+  for (int32_t i = 0; i < n; ++i)
+    if (indeg[i] == 0) ready.push_back(i);
+  size_t head = 0;
+  while (head < ready.size()) {
+    const int32_t i = ready[head++];
+    for (int32_t e = h->row_ptr[i]; e < h->row_ptr[i + 1]; ++e) {
+      const int32_t j = h->col[e];
+      level[j] = std::max(level[j], level[i] + 1);
+      if (--indeg[j] == 0) ready.push_back(j);
+    }
+  }
+  if ((int32_t)ready.size() != n) {
+    delete h;
+    return fail(EULER_ERR_NOT_FEEDFORWARD, "routing graph has a cycle");
+  }
+  h->L = 1 + *std::max_element(level.begin(), level.end());
+  h->lvl_ptr.assign(h->L + 1, 0);
+  for (int32_t i = 0; i < n; ++i) h->lvl_ptr[level[i] + 1]++;
+  for (int32_t j = 0; j < h->L; ++j) h->lvl_ptr[j + 1] += h->lvl_ptr[j];
+  h->lvl_station.assign(n, 0);
+  {
+    std::vector<int32_t> fill(h->lvl_ptr.begin(), h->lvl_ptr.end() - 1);
+    for (int32_t i = 0; i < n; ++i) h->lvl_station[fill[level[i]]++] = i;
+  }
+  h->max_level = 0;
+  for (int32_t j = 0; j < h->L; ++j) h->max_level = std::max(h->max_level, h->lvl_ptr[j + 1] - h->lvl_ptr[j]);
+
+  // conditional split probabilities qc_e = p_e / (p_exit + sum_{e' >= e} p_e')
+  std::vector<float> qc(std::max(h->E, 1), 0.0f);
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t e0 = h->row_ptr[i], e1 = h->row_ptr[i + 1];
+    double rowsum = 0.0;
+    for (int32_t e = e0; e < e1; ++e) rowsum += h->prob[e];
+    double pexit = 1.0 - rowsum;
+    if (pexit < 1e-12) pexit = 0.0;
+    double suffix = pexit;
+    for (int32_t e = e1 - 1; e >= e0; --e) {
+      suffix += h->prob[e];
+      double q = suffix > 0.0 ? h->prob[e] / suffix : 0.0;
+      q = std::min(1.0, std::max(0.0, q));
+      qc[e] = (float)q;
+    }
+  }
+  // reverse graph
+  std::vector<int32_t> in_ptr(n + 1, 0), in_edge(std::max(h->E, 1), 0);
+  for (int32_t e = 0; e < h->E; ++e) in_ptr[h->col[e] + 1]++;
+  for (int32_t i = 0; i < n; ++i) in_ptr[i + 1] += in_ptr[i];
+  {
+    std::vector<int32_t> fill(in_ptr.begin(), in_ptr.end() - 1);
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t e = h->row_ptr[i]; e < h->row_ptr[i + 1]; ++e) in_edge[fill[h->col[e]]++] = e;
+  }
+  // stations with external arrivals
+  h->ex_col.assign(n, -1);
+  for (int32_t i = 0; i < n; ++i) {
+    bool ext = false;
+    if (h->arr_kind == EULER_ARR_SINUSOID) ext = h->w[i] != 0.0 && h->a != 0.0;
+    if (h->arr_kind == EULER_ARR_TABLE)
+      for (int32_t j = 0; j < h->table_len && !ext; ++j) ext = h->table[(int64_t)j * n + i] != 0.0;
+    if (ext) h->ex_col[i] = h->n_ex++;
+  }
+  std::vector<float> mu_f(n);
+  for (int32_t i = 0; i < n; ++i) mu_f[i] = (float)h->mu[i];
+
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e == cudaSuccess) e = upload(&h->d_lvl_ptr, h->lvl_ptr, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_lvl_station, h->lvl_station, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_row_ptr, h->row_ptr, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_in_ptr, in_ptr, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_in_edge, in_edge, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_servers, h->servers, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_N0, h->N0, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_ex_col, h->ex_col, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_qc, qc, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_mu, mu_f, &h->h2d_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    euler_net_destroy(h);
+    return cuda_fail(e, "euler_net_create upload");
+  }
+  *out = h;
+  return EULER_OK;
+}
+
+int64_t euler_net_h2d_bytes(const euler_net* h) { return h ? h->h2d_bytes : -1; }
+
+int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
+  if (!h || option < 0 || option > EULER_OPT_GRAPH_STEPS) return fail(EULER_ERR_ARG, "bad option");
+  h->opt[option] = value < 0 ? -1 : value;
+  return EULER_OK;
+}
+
+int euler_net_plan(euler_net* h, int32_t scheme, int64_t R, int32_t* form, int32_t* tile_reps,
+                   int32_t* block, int32_t* grid, int32_t* smem_bytes) {
+  if (!h || R < 1) return fail(EULER_ERR_ARG, "bad plan arguments");
+  Plan pl;
+  int rc = make_plan(h, scheme, R, &pl);
+  if (rc) return rc;
+  if (form) *form = pl.form;
+  if (tile_reps) *tile_reps = pl.tile_reps;
+  if (block) *block = pl.block;
+  if (grid) *grid = pl.grid;
+  if (smem_bytes) *smem_bytes = (int32_t)pl.smem;
+  return EULER_OK;
+}
+
+int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+                       int64_t rep_begin, int64_t* stats, void* stream) {
+  if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
+  if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return fail(EULER_ERR_ARG, "unknown scheme");
+  if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T)) return fail(EULER_ERR_ARG, "dt and T must be finite and > 0");
+  if (R < 0 || rep_begin < 0 || !stats) return fail(EULER_ERR_ARG, "bad replications, rep_begin or stats");
+  if (rep_begin + R > (int64_t)1 << 32) return fail(EULER_ERR_TOO_LARGE, "replication index beyond 2^32");
+  const int64_t K = euler_num_steps(dt, T);
+  if (K >= (1 << 24)) return fail(EULER_ERR_TOO_LARGE, "too many steps (T/dt >= 2^24)");
+  if (h->n_ex > 0 && K * (int64_t)h->n_ex > ((int64_t)1 << 31)) return fail(EULER_ERR_TOO_LARGE, "arrival table too large");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s));
+  if (R == 0) return EULER_OK;
+  int rc = refresh_step_tables(h, dt, T, s);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(h, scheme, R, &pl);
+  if (rc) return rc;
+  RunParams p;
+  p.p0 = h->d_p0;
+  p.lam = h->d_lam;
+  p.h = (float)dt;
+  p.K = (int32_t)K;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.R = R;
+  p.rep_begin = rep_begin;
+  p.scheme = scheme;
+  p.tile_reps = pl.tile_reps;
+  p.num_tiles = pl.num_tiles;
+  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+  p.stats = stats;
+  p.err = h->d_err;
+  const NetTables t = h->tables();
+  if (pl.form == 1) {
+    cudaError_t e = launch_persistent(t, p, pl.grid, pl.block, (int)pl.smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+    return EULER_OK;
+  }
+  return run_hbm(h, t, p, pl, s);
+}
+
+int euler_net_status(euler_net* h, void* stream) {
+  if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  unsigned bits = 0;
+  CUDA_TRY(cudaMemcpy(&bits, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(unsigned)));
+  if (bits & kErrSamplerCap) return fail(EULER_ERR_SAMPLER_CAP, "a sampler rejection loop hit its cap");
+  if (bits & kErrOverflow) return fail(EULER_ERR_OVERFLOW, "a station count exceeded 2^30");
+  return EULER_OK;
+}
+
+int euler_net_simulate_host(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
+                            uint64_t seed, int64_t rep_begin, int64_t* stats_host, void* stream) {
+  if (!h || !stats_host) return fail(EULER_ERR_ARG, "handle or stats is NULL");
+  const size_t bytes = sizeof(int64_t) * (size_t)euler_stats_len(h->n, R);
+  int64_t* d_stats = nullptr;
+  CUDA_TRY(cudaMalloc(&d_stats, bytes));
+  int rc = euler_net_simulate(h, scheme, dt, T, R, seed, rep_begin, d_stats, stream);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (rc == EULER_OK) {
+    cudaError_t e = cudaMemcpyAsync(stats_host, d_stats, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "stats copy");
+  }
+  const int st = euler_net_status(h, stream);
+  cudaFree(d_stats);
+  return rc ? rc : st;
+}
+
+}  // extern "C"

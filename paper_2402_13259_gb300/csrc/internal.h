@@ -1,0 +1,75 @@
+// internal.h -- device table layout and launch entry points shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace eulernet {
+
+// Immutable network tables on the device (uploaded once by euler_net_create).
+struct NetTables {
+  int32_t n;          // stations
+  int32_t E;          // edges (CSR nnz)
+  int32_t L;          // levels (longest-path depth + 1)
+  int32_t max_level;  // stations in the widest level
+  const int32_t* lvl_ptr;      // [L+1] offsets into lvl_station
+  const int32_t* lvl_station;  // [n] stations ordered by (level, index)
+  const int32_t* row_ptr;      // [n+1] CSR (routing P)
+  const float* qc;             // [E] conditional split probability of each edge
+  const int32_t* in_ptr;       // [n+1] CSC offsets (edges into each station)
+  const int32_t* in_edge;      // [E] edge ids into each station
+  const int32_t* servers;      // [n] m_i
+  const float* mu;             // [n] mu_i rounded to float
+  const int32_t* N0;           // [n] or nullptr
+  const int32_t* ex_col;       // [n] column of the station in the Lambda table, or -1
+  int32_t n_ex;                // stations with external arrivals
+};
+
+// Per-call parameters.
+struct RunParams {
+  const float* p0;   // [n] 1 - e^{-mu_i dt}
+  const float* lam;  // [K][n_ex] per-step arrival means
+  float h;           // dt rounded to float
+  int32_t K;         // steps
+  uint32_t key0, key1;
+  int64_t R;          // replications in this call
+  int64_t rep_begin;  // global index of local replication 0
+  int32_t scheme;     // 0 backward, 1 forward
+  int32_t tile_reps;  // replications per tile (power of two)
+  int64_t num_tiles;
+  int32_t cap;        // rejection-loop cap
+  int64_t* stats;     // output, see eulernet.h
+  unsigned* err;      // latched error bits
+};
+
+// Shared-memory bytes of the persistent kernel for a tile of `tile_reps`.
+int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps);
+
+// Launch the persistent shared-memory kernel.
+cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block,
+                              int smem, cudaStream_t s);
+
+// Blocks of `block` threads with `smem` bytes that fit on one SM.
+cudaError_t persistent_occupancy(int block, int smem, int* blocks_per_sm);
+
+// HBM-state form: per-step kernels over state in global memory.
+struct HbmState {
+  int32_t* N;      // [n][R] station-major, replication-fastest
+  int32_t* Redge;  // [E][R]
+  int64_t* racc;   // [R][4] per-replication partial sums
+  int32_t* tau;    // device step counter (1-based)
+  int64_t ld;      // leading dimension (>= R, multiple of 4)
+};
+int64_t hbm_smem_bytes(int32_t n, int32_t tile_reps);
+cudaError_t launch_hbm_init(const NetTables& t, const RunParams& p, const HbmState& hs,
+                            cudaStream_t s);
+// One step's kernels (backward: 2 phases; forward: one per level), then the
+// step counter advance.  Safe to capture in a CUDA graph.
+cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
+                            const int32_t* lvl_ptr_host, cudaStream_t s);
+cudaError_t launch_hbm_finish(const NetTables& t, const RunParams& p, const HbmState& hs,
+                              cudaStream_t s);
+
+}  // namespace eulernet

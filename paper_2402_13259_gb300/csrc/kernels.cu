@@ -1,0 +1,487 @@
+// kernels.cu -- the Euler step of arXiv 2402.13259 on sm_103a.
+//
+// Two forms of the same step (results identical bit for bit):
+//  * persistent: one CTA owns a tile of replications, keeps the whole network
+//    state of the tile (N and the routed edge counts R_e) in shared memory and
+//    runs the time loop inside the kernel; CTAs loop over tiles.
+//  * hbm: state in global memory (station-major, replication-fastest), one
+//    kernel per phase of a step, the step loop captured in a CUDA graph; used
+//    when a tile does not fit in shared memory.
+//
+// One "unit" is one (station, replication) update of one step:
+//   backward (Sec. 2.2 tasks 1-4, Algorithm 2): D from N_{tau-1}, routing,
+//     external arrivals for every station, then -- after a block barrier --
+//     the gather of routed counts over the reverse graph (CSC) and the update;
+//   forward (Sec. 2.2 tasks 1-4, Algorithm 3): level by level in flow order,
+//     gather, external arrivals, D from N_{tau-1} + A^ex + A^in, update,
+//     routing; a barrier between levels.
+// Thread mapping: thread t owns replication slot r = t % Rt of the tile and
+// station slots t / Rt + k G (G = blockDim / Rt), so lanes with consecutive r
+// share a station: per-station sums are warp-segmented reductions and
+// per-replication sums stay in registers.
+#include <cstdint>
+
+#include "internal.h"
+#include "sampling.cuh"
+
+namespace eulernet {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void latch(unsigned* err, unsigned bits) {
+  if (bits) atomicOr(err, bits);
+}
+
+// Sequential conditional binomials along the CSR row (Sec. 2.2 multinomial).
+__device__ __forceinline__ int32_t route_row(int32_t D, int32_t e0, int32_t e1, const float* qc,
+                                             int32_t* redge, int64_t stride, int64_t col,
+                                             PhiloxStream& st, SamplerCtx& cx) {
+  int32_t rem = D;
+  for (int32_t e = e0; e < e1; ++e) {
+    int32_t v = 0;
+    if (rem > 0) v = binomial(rem, __ldg(qc + e), st, cx);
+    redge[(int64_t)e * stride + col] = v;
+    rem = rem - v;
+  }
+  return rem;
+}
+
+__device__ __forceinline__ int64_t gather_in(const NetTables& t, int32_t i, const int32_t* redge,
+                                             int64_t stride, int64_t col) {
+  int64_t s = 0;
+  const int32_t k1 = __ldg(t.in_ptr + i + 1);
+  for (int32_t k = __ldg(t.in_ptr + i); k < k1; ++k)
+    s += redge[(int64_t)__ldg(t.in_edge + k) * stride + col];
+  return s;
+}
+
+// Sum `v` over aligned segments of `w` lanes (w a power of two <= 32); the
+// segment total ends up in every lane of the segment.
+__device__ __forceinline__ unsigned seg_sum32(unsigned v, int w) {
+  if (w == 32) return __reduce_add_sync(kFull, v);
+  for (int off = w >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+__device__ __forceinline__ long long seg_sum64(long long v, int w) {
+  for (int off = w >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+// Reduce NV per-unit values over the replication segment and add them to
+// dst[0..NV) by the segment leader.  `fits` must be warp-uniform-safe: it is
+// combined with __all_sync here.  mode 0: plain add (exclusive owner), 1:
+// shared/global atomic add.
+template <int NV>
+__device__ __forceinline__ void reduce_to(long long* dst, const int32_t (&v)[NV], bool lead,
+                                          int w, bool atomic) {
+  int32_t vmax = 0;
+#pragma unroll
+  for (int s = 0; s < NV; ++s) vmax = v[s] > vmax ? v[s] : vmax;
+  const bool small = __all_sync(kFull, vmax < (1 << 27));
+  long long tot[NV];
+  if (small) {
+#pragma unroll
+    for (int s = 0; s < NV; ++s) tot[s] = (long long)seg_sum32((unsigned)v[s], w);
+  } else {
+#pragma unroll
+    for (int s = 0; s < NV; ++s) tot[s] = seg_sum64((long long)v[s], w);
+  }
+  if (lead) {
+#pragma unroll
+    for (int s = 0; s < NV; ++s) {
+      if (atomic)
+        atomicAdd(reinterpret_cast<unsigned long long*>(dst + s), (unsigned long long)tot[s]);
+      else
+        dst[s] += tot[s];
+    }
+  }
+}
+
+// ---- one unit of each scheme -------------------------------------------------
+
+struct UnitOut {
+  int32_t N, D, X, A;
+};
+
+// Backward phase 1 at station i: D from N_{tau-1}, routing, external arrivals;
+// stores N_{tau-1} - D + A^ex (the gather is added in phase 2).
+__device__ __forceinline__ UnitOut backward_departures(const NetTables& t, const RunParams& p,
+                                                       int32_t i, uint32_t tau, uint32_t rep,
+                                                       const float* lam_t, int32_t* nstate,
+                                                       int32_t* redge, int64_t stride,
+                                                       int64_t col, SamplerCtx& cx) {
+  UnitOut o;
+  const int32_t x = nstate[(int64_t)i * stride + col];
+  PhiloxStream svc;
+  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
+  o.D = generate_departure(x, __ldg(t.servers + i), __ldg(t.mu + i), p.h, __ldg(p.p0 + i), svc, cx);
+  o.X = route_row(o.D, __ldg(t.row_ptr + i), __ldg(t.row_ptr + i + 1), t.qc, redge, stride, col, svc,
+                  cx);
+  o.A = 0;
+  const int32_t ec = __ldg(t.ex_col + i);
+  if (ec >= 0) {
+    PhiloxStream arr;
+    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
+    o.A = poisson(__ldg(lam_t + ec), arr, cx);
+  }
+  long long part = (long long)x - o.D + o.A;
+  if (part > 0x7fffffffLL) part = 0x7fffffffLL;
+  nstate[(int64_t)i * stride + col] = (int32_t)part;
+  o.N = 0;
+  return o;
+}
+
+// Backward phase 2: N_tau = (N_{tau-1} - D + A^ex) + A^in.
+__device__ __forceinline__ int32_t backward_gather(const NetTables& t, int32_t i, int32_t* nstate,
+                                                   const int32_t* redge, int64_t stride,
+                                                   int64_t col, unsigned& err) {
+  long long nn = (long long)nstate[(int64_t)i * stride + col] + gather_in(t, i, redge, stride, col);
+  if (nn > kStateLimit) {
+    err |= kErrOverflow;
+    nn = kStateLimit;
+  }
+  nstate[(int64_t)i * stride + col] = (int32_t)nn;
+  return (int32_t)nn;
+}
+
+// Forward unit at station i (its upstream stations are already done).
+__device__ __forceinline__ UnitOut forward_unit(const NetTables& t, const RunParams& p, int32_t i,
+                                                uint32_t tau, uint32_t rep, const float* lam_t,
+                                                int32_t* nstate, int32_t* redge, int64_t stride,
+                                                int64_t col, SamplerCtx& cx) {
+  UnitOut o;
+  o.A = 0;
+  const int32_t ec = __ldg(t.ex_col + i);
+  if (ec >= 0) {
+    PhiloxStream arr;
+    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
+    o.A = poisson(__ldg(lam_t + ec), arr, cx);
+  }
+  long long y = (long long)nstate[(int64_t)i * stride + col] + o.A + gather_in(t, i, redge, stride, col);
+  if (y > kStateLimit) {
+    cx.err |= kErrOverflow;
+    y = kStateLimit;
+  }
+  PhiloxStream svc;
+  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
+  o.D = generate_departure((int32_t)y, __ldg(t.servers + i), __ldg(t.mu + i), p.h, __ldg(p.p0 + i),
+                           svc, cx);
+  o.N = (int32_t)y - o.D;
+  nstate[(int64_t)i * stride + col] = o.N;
+  o.X = route_row(o.D, __ldg(t.row_ptr + i), __ldg(t.row_ptr + i + 1), t.qc, redge, stride, col, svc,
+                  cx);
+  return o;
+}
+
+__device__ __forceinline__ void fill_rinv(float* rinv) {
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) rinv[k] = k ? 1.0f / (float)k : 0.0f;
+}
+
+// ---- persistent shared-memory kernel -----------------------------------------
+
+// Shared layout: rinv[64] f32 | sacc[n][6] i64 | racc[Rt][4] i64 | N[n][Rt] i32 | Redge[E][Rt] i32
+__global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int32_t n = t.n;
+  const int Rt = p.tile_reps;
+  float* rinv = reinterpret_cast<float*>(smem);
+  long long* sacc = reinterpret_cast<long long*>(smem + 256);
+  long long* racc = sacc + 6 * (int64_t)n;
+  int32_t* Ns = reinterpret_cast<int32_t*>(racc + 4 * (int64_t)Rt);
+  int32_t* Rs = Ns + (int64_t)n * Rt;
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int r = tid % Rt;
+  const int g0 = tid / Rt;
+  const int G = nthr / Rt;
+  const int lane = tid & 31;
+  const int w = Rt < 32 ? Rt : 32;
+  const int gwarp = (tid & ~31) / Rt;  // group of lane 0 of this warp
+  const bool lead = (lane & (w - 1)) == 0;
+  const bool shared_station = Rt > 32;  // several warps per station -> atomics
+
+  fill_rinv(rinv);
+  for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sacc[k] = 0;
+  SamplerCtx cx{rinv, p.cap, 0u};
+  __syncthreads();
+
+  for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+    const int64_t rloc = tile * Rt + r;
+    const bool rvalid = rloc < p.R;
+    const uint32_t rep = (uint32_t)(p.rep_begin + rloc);
+    for (int64_t k = tid; k < (int64_t)n * Rt; k += nthr)
+      Ns[k] = t.N0 ? __ldg(t.N0 + k / Rt) : 0;
+    for (int k = tid; k < 4 * Rt; k += nthr) racc[k] = 0;
+    long long q_r = 0, d_r = 0, x_r = 0, a_r = 0;
+    __syncthreads();
+
+    for (int32_t tau = 1; tau <= p.K; ++tau) {
+      const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
+      if (p.scheme == 0) {
+        for (int su0 = gwarp; su0 < n; su0 += G) {
+          const int su = su0 + (g0 - gwarp);
+          const bool act = rvalid && su < n;
+          int32_t v[3] = {0, 0, 0};
+          if (act) {
+            UnitOut o = backward_departures(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+            v[0] = o.D;
+            v[1] = o.X;
+            v[2] = o.A;
+            d_r += o.D;
+            x_r += o.X;
+            a_r += o.A;
+          }
+          reduce_to<3>(sacc + 6 * (int64_t)(su < n ? su : 0) + 2, v, lead && su < n, w,
+                       shared_station);
+        }
+        __syncthreads();
+        for (int su0 = gwarp; su0 < n; su0 += G) {
+          const int su = su0 + (g0 - gwarp);
+          const bool act = rvalid && su < n;
+          int32_t v[2] = {0, 0};
+          if (act) {
+            const int32_t nn = backward_gather(t, su, Ns, Rs, Rt, r, cx.err);
+            const int32_t c = __ldg(t.servers + su);
+            v[0] = nn;
+            v[1] = nn < c ? nn : c;
+            q_r += nn;
+          }
+          reduce_to<2>(sacc + 6 * (int64_t)(su < n ? su : 0), v, lead && su < n, w, shared_station);
+        }
+        __syncthreads();
+      } else {
+        for (int32_t j = 0; j < t.L; ++j) {
+          const int32_t s0 = __ldg(t.lvl_ptr + j);
+          const int32_t m = __ldg(t.lvl_ptr + j + 1) - s0;
+          for (int su0 = gwarp; su0 < m; su0 += G) {
+            const int su = su0 + (g0 - gwarp);
+            const bool act = rvalid && su < m;
+            const int32_t i = su < m ? __ldg(t.lvl_station + s0 + su) : 0;
+            int32_t v[5] = {0, 0, 0, 0, 0};
+            if (act) {
+              UnitOut o = forward_unit(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+              const int32_t c = __ldg(t.servers + i);
+              v[0] = o.N;
+              v[1] = o.N < c ? o.N : c;
+              v[2] = o.D;
+              v[3] = o.X;
+              v[4] = o.A;
+              q_r += o.N;
+              d_r += o.D;
+              x_r += o.X;
+              a_r += o.A;
+            }
+            reduce_to<5>(sacc + 6 * (int64_t)i, v, lead && su < m, w, shared_station);
+          }
+          __syncthreads();
+        }
+      }
+    }
+
+    // tile epilogue: per-replication sums and N_K
+    if (rvalid) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 0), (unsigned long long)q_r);
+      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 1), (unsigned long long)d_r);
+      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 2), (unsigned long long)x_r);
+      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 3), (unsigned long long)a_r);
+    }
+    for (int su0 = gwarp; su0 < n; su0 += G) {
+      const int su = su0 + (g0 - gwarp);
+      int32_t v[1] = {(rvalid && su < n) ? Ns[(int64_t)su * Rt + r] : 0};
+      reduce_to<1>(sacc + 6 * (int64_t)(su < n ? su : 0) + 5, v, lead && su < n, w, shared_station);
+    }
+    __syncthreads();
+    int64_t* st_rep = p.stats + 5 * (int64_t)n;
+    for (int k = tid; k < 4 * Rt; k += nthr) {
+      const int64_t rr = tile * Rt + k / 4;
+      if (rr < p.R) st_rep[rr * 4 + (k & 3)] = racc[k];
+    }
+    __syncthreads();
+  }
+
+  // kernel epilogue: per-station sums
+  int64_t* st_nk = p.stats + 5 * (int64_t)n + 4 * p.R;
+  for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) {
+    const int64_t i = k / 6, s = k % 6;
+    const long long v = sacc[k];
+    if (v == 0) continue;
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(
+        s < 5 ? p.stats + i * 5 + s : st_nk + i);
+    atomicAdd(dst, (unsigned long long)v);
+  }
+  latch(p.err, cx.err);
+}
+
+// ---- HBM-state form -------------------------------------------------------------
+
+constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
+
+// Units of one phase over stations lvl_station[s0 .. s0+m) (or 0..n when
+// all == true).  Grid: x over replication tiles of 32, y over station chunks.
+__global__ void __launch_bounds__(256) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
+                                                        int32_t phase, int32_t s0, int32_t m) {
+  __shared__ float rinv[64];
+  __shared__ long long racc_s[kHbmTile * 4];
+  const int32_t tau = *hs.tau;
+  if (tau > p.K) return;  // uniform: steps past the horizon are no-ops
+  const int tid = threadIdx.x;
+  fill_rinv(rinv);
+  for (int k = tid; k < kHbmTile * 4; k += blockDim.x) racc_s[k] = 0;
+  __syncthreads();
+  const int r = tid % kHbmTile;
+  const int G = blockDim.x / kHbmTile;
+  const int su = blockIdx.y * G + tid / kHbmTile;
+  const int64_t rloc = (int64_t)blockIdx.x * kHbmTile + r;
+  const bool act = rloc < p.R && su < m;
+  const bool lead = (tid & 31) == 0;
+  const int32_t i = su < m ? (phase == 2 ? __ldg(t.lvl_station + s0 + su) : su) : 0;
+  const uint32_t rep = (uint32_t)(p.rep_begin + rloc);
+  const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
+  SamplerCtx cx{rinv, p.cap, 0u};
+  long long* st = reinterpret_cast<long long*>(p.stats + 5 * (int64_t)i);
+  int32_t part[4] = {0, 0, 0, 0};  // Q, D, X, A per replication
+  if (phase == 0) {  // backward departures / routing / arrivals
+    int32_t v[3] = {0, 0, 0};
+    if (act) {
+      UnitOut o = backward_departures(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
+      v[0] = o.D; v[1] = o.X; v[2] = o.A;
+      part[1] = o.D; part[2] = o.X; part[3] = o.A;
+    }
+    reduce_to<3>(st + 2, v, lead && su < m, 32, true);
+  } else if (phase == 1) {  // backward gather / update
+    int32_t v[2] = {0, 0};
+    if (act) {
+      const int32_t nn = backward_gather(t, i, hs.N, hs.Redge, hs.ld, rloc, cx.err);
+      const int32_t c = __ldg(t.servers + i);
+      v[0] = nn; v[1] = nn < c ? nn : c;
+      part[0] = nn;
+    }
+    reduce_to<2>(st, v, lead && su < m, 32, true);
+  } else {  // forward level
+    int32_t v[5] = {0, 0, 0, 0, 0};
+    if (act) {
+      UnitOut o = forward_unit(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
+      const int32_t c = __ldg(t.servers + i);
+      v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
+      part[0] = o.N; part[1] = o.D; part[2] = o.X; part[3] = o.A;
+    }
+    reduce_to<5>(st, v, lead && su < m, 32, true);
+  }
+  if (act) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (part[s])
+        atomicAdd(reinterpret_cast<unsigned long long*>(racc_s + 4 * r + s), (unsigned long long)part[s]);
+  }
+  __syncthreads();
+  for (int k = tid; k < kHbmTile * 4; k += blockDim.x) {
+    const int64_t rr = (int64_t)blockIdx.x * kHbmTile + k / 4;
+    if (rr < p.R && racc_s[k] != 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(hs.racc + rr * 4 + (k & 3)),
+                (unsigned long long)racc_s[k]);
+  }
+  latch(p.err, cx.err);
+}
+
+__global__ void hbm_advance_kernel(int32_t* tau) { *tau += 1; }
+
+__global__ void hbm_init_kernel(NetTables t, RunParams p, HbmState hs) {
+  const int64_t total = (int64_t)t.n * hs.ld;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x)
+    hs.N[k] = t.N0 ? __ldg(t.N0 + k / hs.ld) : 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * p.R;
+       k += (int64_t)gridDim.x * blockDim.x)
+    hs.racc[k] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hs.tau = 1;
+}
+
+// Per-replication sums out, and N_K summed over replications (one block per
+// station, 128-bit loads of the replication-fastest state).
+__global__ void hbm_finish_kernel(NetTables t, RunParams p, HbmState hs) {
+  int64_t* st_rep = p.stats + 5 * (int64_t)t.n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * p.R;
+       k += (int64_t)gridDim.x * blockDim.x)
+    st_rep[k] = hs.racc[k];
+  __shared__ long long part[32];
+  for (int32_t i = blockIdx.x; i < t.n; i += gridDim.x) {
+    const int4* row = reinterpret_cast<const int4*>(hs.N + (int64_t)i * hs.ld);
+    long long s = 0;
+    const int64_t nvec = p.R / 4;
+    for (int64_t k = threadIdx.x; k < nvec; k += blockDim.x) {
+      const int4 q = row[k];
+      s += (long long)q.x + q.y + q.z + q.w;
+    }
+    for (int64_t k = nvec * 4 + threadIdx.x; k < p.R; k += blockDim.x) s += hs.N[(int64_t)i * hs.ld + k];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long tot = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += part[k];
+      p.stats[5 * (int64_t)t.n + 4 * p.R + i] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps) {
+  return 256 + 6 * 8 * (int64_t)n + 4 * 8 * (int64_t)tile_reps +
+         4 * ((int64_t)n + E) * tile_reps;
+}
+
+cudaError_t persistent_occupancy(int block, int smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel, block, smem);
+}
+
+cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block, int smem,
+                              cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  persistent_kernel<<<grid, block, smem, s>>>(t, p);
+  return cudaGetLastError();
+}
+
+int64_t hbm_smem_bytes(int32_t, int32_t) { return 0; }
+
+cudaError_t launch_hbm_init(const NetTables& t, const RunParams& p, const HbmState& hs,
+                            cudaStream_t s) {
+  hbm_init_kernel<<<1024, 256, 0, s>>>(t, p, hs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
+                            const int32_t* lvl_ptr_host, cudaStream_t s) {
+  const int G = block / kHbmTile;
+  const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
+  if (p.scheme == 0) {
+    dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
+    hbm_phase_kernel<<<grid, block, 0, s>>>(t, p, hs, 0, 0, t.n);
+    hbm_phase_kernel<<<grid, block, 0, s>>>(t, p, hs, 1, 0, t.n);
+  } else {
+    for (int32_t j = 0; j < t.L; ++j) {
+      const int32_t s0 = lvl_ptr_host[j], m = lvl_ptr_host[j + 1] - lvl_ptr_host[j];
+      dim3 grid(tiles, (unsigned)((m + G - 1) / G));
+      hbm_phase_kernel<<<grid, block, 0, s>>>(t, p, hs, 2, s0, m);
+    }
+  }
+  hbm_advance_kernel<<<1, 1, 0, s>>>(hs.tau);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_finish(const NetTables& t, const RunParams& p, const HbmState& hs,
+                              cudaStream_t s) {
+  hbm_finish_kernel<<<t.n < 1024 ? t.n : 1024, 256, 0, s>>>(t, p, hs);
+  return cudaGetLastError();
+}
+
+}  // namespace eulernet

@@ -1,0 +1,441 @@
+// sampling.cuh -- random streams, float32 elementary functions and samplers
+// of the Euler step (arXiv 2402.13259), for sm_103a.
+//
+// Every function evaluates a fixed sequence of correctly rounded IEEE float
+// operations (the library is compiled with -fmad=false -prec-div=true
+// -prec-sqrt=true -ftz=false; fused multiply-adds appear only where fmaf is
+// written), so a replication's integer trajectory is a pure function of
+// (seed, replication, step, station).  The definitions:
+//   stream   Philox4x32-10, key = (seed lo, seed hi), counter =
+//            (purpose << 24 | block, station, step, replication); purpose 0 =
+//            external arrivals, 1 = service (departure, then routing edges in
+//            CSR order); words consumed in order.
+//   uniform  u = (2 (w >> 9) + 1) 2^-24, exact, in [2^-24, 1 - 2^-24].
+//   exp/log/expm1/log1p  argument reduction + truncated Taylor/atanh series.
+//   Poisson  inversion for lambda < 10, PTRS (Hoermann 1993) otherwise.
+//   Binomial symmetric for p > 1/2; inversion for n p < 10, BTRS (Hoermann
+//            1993) otherwise, with Loader's (2000) exact log-pmf.
+//   Erlang   minus log of products of <= 4 uniforms for shape <= 8,
+//            Marsaglia-Tsang (2000) with polar normals otherwise.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define EN_HD __host__ __device__ __forceinline__
+#define EN_D __device__ __forceinline__
+#else
+#define EN_HD inline
+#define EN_D inline
+#endif
+
+namespace eulernet {
+
+// Error bits latched in the handle's device error word.
+constexpr unsigned kErrSamplerCap = 1u;
+constexpr unsigned kErrOverflow = 2u;
+constexpr int32_t kStateLimit = 1 << 30;
+
+EN_HD float bits_f(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(u);
+#else
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+EN_HD uint32_t f_bits(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(f);
+#else
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// Float32 elementary functions.
+// ---------------------------------------------------------------------------
+namespace fm {
+
+constexpr float kLn2Hi = 0x1.62e400p-1f;  // ln 2 with 9 trailing zero bits
+constexpr float kLn2Lo = 0x1.7f7d1cp-20f;  // ln 2 - kLn2Hi
+constexpr float kLog2e = 0x1.715476p+0f;
+constexpr float kSqrt2 = 0x1.6a09e6p+0f;
+constexpr float kLn2Pi = 0x1.d67f1cp+0f;   // ln(2 pi)
+
+EN_HD float inf() { return bits_f(0x7f800000u); }
+EN_HD float qnan() { return bits_f(0x7fc00000u); }
+
+// e^x = 2^k e^r, k = floor(x log2e + 1/2), r = x - k ln2 in two parts;
+// e^r by its degree-7 Taylor polynomial in Horner form.
+EN_HD float exp(float x) {
+  if (x != x) return x;
+  if (x > 88.72283935546875f) return inf();
+  if (x < -103.97207641601562f) return 0.0f;
+  const float k = floorf(x * kLog2e + 0.5f);
+  float r = fmaf(-k, kLn2Hi, x);
+  r = fmaf(-k, kLn2Lo, r);
+  float s = (float)(1.0 / 5040.0);
+  s = fmaf(s, r, (float)(1.0 / 720.0));
+  s = fmaf(s, r, (float)(1.0 / 120.0));
+  s = fmaf(s, r, (float)(1.0 / 24.0));
+  s = fmaf(s, r, (float)(1.0 / 6.0));
+  s = fmaf(s, r, 0.5f);
+  s = fmaf(s, r, 1.0f);
+  s = fmaf(s, r, 1.0f);
+  const int ki = (int)k;
+  if (ki < -125) return (s * bits_f((uint32_t)(ki + 227) << 23)) * 0x1p-100f;
+  if (ki > 127) return (s * bits_f((uint32_t)(ki + 126) << 23)) * 2.0f;
+  return s * bits_f((uint32_t)(ki + 127) << 23);
+}
+
+// ln x = e ln2 + ln(1+f), 1+f in [sqrt(1/2), sqrt(2)); with s = f/(2+f),
+// ln(1+f) = 2 atanh s = f - s f + 2 s (s^2/3 + s^4/5 + s^6/7 + s^8/9).
+EN_HD float log(float x) {
+  if (x != x) return x;
+  if (x < 0.0f) return qnan();
+  if (x == 0.0f) return -inf();
+  if (x == inf()) return x;
+  int bias = 0;
+  if (x < 0x1p-126f) {
+    x = x * 0x1p25f;
+    bias = -25;
+  }
+  const uint32_t b = f_bits(x);
+  int e = (int)(b >> 23) - 127 + bias;
+  float m = bits_f((b & 0x007fffffu) | 0x3f800000u);
+  if (m > kSqrt2) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  const float f = m - 1.0f;
+  const float s = f / (2.0f + f);
+  const float z = s * s;
+  float t = (float)(1.0 / 9.0);
+  t = fmaf(t, z, (float)(1.0 / 7.0));
+  t = fmaf(t, z, (float)(1.0 / 5.0));
+  t = fmaf(t, z, (float)(1.0 / 3.0));
+  t = t * z;
+  const float sf = s * f;
+  const float corr = fmaf(2.0f * s, t, -sf);
+  const float lm = f + corr;
+  const float ef = (float)e;
+  const float lo = fmaf(ef, kLn2Lo, lm);
+  return fmaf(ef, kLn2Hi, lo);
+}
+
+// e^x - 1: Taylor to degree 8 below ln2/2 in magnitude, else exp(x) - 1.
+EN_HD float expm1(float x) {
+  if (fabsf(x) < 0.3465735912322998f) {
+    float s = (float)(1.0 / 40320.0);
+    s = fmaf(s, x, (float)(1.0 / 5040.0));
+    s = fmaf(s, x, (float)(1.0 / 720.0));
+    s = fmaf(s, x, (float)(1.0 / 120.0));
+    s = fmaf(s, x, (float)(1.0 / 24.0));
+    s = fmaf(s, x, (float)(1.0 / 6.0));
+    s = fmaf(s, x, 0.5f);
+    return fmaf(x * s, x, x);
+  }
+  return fm::exp(x) - 1.0f;
+}
+
+// ln(1+x) = ln(u) * x / (u - 1), u = 1 + x rounded (Goldberg 1991).
+EN_HD float log1p(float x) {
+  const float u = 1.0f + x;
+  if (u == 1.0f) return x;
+  return fm::log(u) * (x / (u - 1.0f));
+}
+
+}  // namespace fm
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 stream.
+// ---------------------------------------------------------------------------
+struct PhiloxStream {
+  uint32_t key0, key1;
+  uint32_t ctr0, ctr1, ctr2, ctr3;  // ctr0 holds purpose << 24; block is OR-ed in
+  uint32_t w0, w1, w2, w3;          // buffered words, consumed w0 first
+  uint32_t left;                    // words remaining in the buffer
+  uint32_t block;                   // next block index
+
+  EN_D void init(uint32_t k0, uint32_t k1, uint32_t purpose, uint32_t station, uint32_t step,
+                 uint32_t rep) {
+    key0 = k0;
+    key1 = k1;
+    ctr0 = purpose << 24;
+    ctr1 = station;
+    ctr2 = step;
+    ctr3 = rep;
+    left = 0;
+    block = 0;
+  }
+
+  EN_D void refill() {
+    uint32_t x0 = ctr0 | block, x1 = ctr1, x2 = ctr2, x3 = ctr3;
+    uint32_t k0 = key0, k1 = key1;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+      const uint32_t lo0 = 0xD2511F53u * x0;
+      const uint32_t hi0 = __umulhi(0xD2511F53u, x0);
+      const uint32_t lo1 = 0xCD9E8D57u * x2;
+      const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2);
+      const uint32_t y0 = hi1 ^ x1 ^ k0;
+      const uint32_t y2 = hi0 ^ x3 ^ k1;
+      x0 = y0;
+      x1 = lo1;
+      x2 = y2;
+      x3 = lo0;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    w0 = x0;
+    w1 = x1;
+    w2 = x2;
+    w3 = x3;
+    left = 4;
+    ++block;
+  }
+
+  EN_D uint32_t next() {
+    if (left == 0) refill();
+    const uint32_t w = w0;
+    w0 = w1;
+    w1 = w2;
+    w2 = w3;
+    --left;
+    return w;
+  }
+
+  EN_D float uniform() {
+    const uint32_t w = next();
+    const uint32_t odd = ((w >> 9) << 1) | 1u;
+    return (float)odd * 0x1p-24f;
+  }
+};
+
+// Per-launch sampler context: reciprocal table 1/k (k < 64) in shared memory,
+// rejection cap, latched error bits.
+struct SamplerCtx {
+  const float* rinv;
+  int cap;
+  unsigned err;
+};
+
+// ---------------------------------------------------------------------------
+// Exact log-probabilities (Loader 2000): Stirling error and deviance bd0.
+// ---------------------------------------------------------------------------
+EN_D float log_small_factorial(int k) {  // k <= 9, k! exact in float
+  float f = 1.0f;
+  for (int j = 2; j <= k; ++j) f = f * (float)j;
+  return fm::log(f);
+}
+
+EN_D float stirling_err(float k) {
+  if (k < 10.0f) {
+    float t = (k + 0.5f) * fm::log(k);
+    t = t - k;
+    t = t + 0.5f * fm::kLn2Pi;
+    return log_small_factorial((int)k) - t;
+  }
+  const float k2 = k * k;
+  float s = (float)(1.0 / 1260.0) / k2;
+  s = (float)(1.0 / 360.0) - s;
+  s = s / k2;
+  s = (float)(1.0 / 12.0) - s;
+  return s / k;
+}
+
+EN_D float deviance(float x, float m) {  // x ln(x/m) + m - x
+  if (x == 0.0f) return m;
+  const float d = x - m;
+  if (fabsf(d) < 0.1f * (x + m)) {
+    const float v = d / (x + m);
+    float s = d * v;
+    float ej = 2.0f * x * v;
+    const float v2 = v * v;
+#pragma unroll
+    for (int j = 1; j <= 5; ++j) {
+      ej = ej * v2;
+      s = s + ej / (float)(2 * j + 1);
+    }
+    return s;
+  }
+  return x * fm::log(x / m) + m - x;
+}
+
+EN_D float log_pois_pmf(int k, float lam) {
+  if (k == 0) return -lam;
+  const float kf = (float)k;
+  if (k < 10) return kf * fm::log(lam) - lam - log_small_factorial(k);
+  const float t = fm::kLn2Pi + fm::log(kf);
+  float r = -0.5f * t;
+  r = r - stirling_err(kf);
+  return r - deviance(kf, lam);
+}
+
+EN_D float log_binom_pmf(int k, int n, float p, float q) {
+  const float nf = (float)n;
+  if (k == 0) return nf * fm::log1p(-p);
+  if (k == n) return nf * fm::log(p);
+  const float kf = (float)k;
+  const float rf = (float)(n - k);
+  const float lc = stirling_err(nf) - stirling_err(kf) - stirling_err(rf) - deviance(kf, nf * p) -
+                   deviance(rf, nf * q);
+  const float lf = fm::kLn2Pi + fm::log(kf) + fm::log1p(-(kf / nf));
+  return lc - 0.5f * lf;
+}
+
+// ---------------------------------------------------------------------------
+// Samplers.
+// ---------------------------------------------------------------------------
+EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
+  if (!(lam > 0.0f)) return 0;
+  if (lam < 10.0f) {
+    const float u = st.uniform();
+    float p = fm::exp(-lam);
+    float F = p;
+    int32_t k = 0;
+    while (u > F) {
+      if (k == 63) break;
+      k = k + 1;
+      p = (p * lam) * cx.rinv[k];
+      const float Fn = F + p;
+      if (Fn == F) break;
+      F = Fn;
+    }
+    return k;
+  }
+  const float slam = sqrtf(lam);
+  const float b = 0.931f + 2.53f * slam;
+  const float a = -0.059f + 0.02483f * b;
+  const float inv_alpha = 1.1239f + 1.1328f / (b - 3.4f);
+  const float vr = 0.9277f - 3.6224f / (b - 2.0f);
+  for (int it = 0; it < cx.cap; ++it) {
+    const float U = st.uniform() - 0.5f;
+    const float V = st.uniform();
+    const float us = 0.5f - fabsf(U);
+    const float kf = floorf((2.0f * a / us + b) * U + lam + 0.43f);
+    if (us >= 0.07f && V <= vr) return (int32_t)kf;
+    if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+    if (kf > 1.0e9f) continue;
+    const int32_t k = (int32_t)kf;
+    const float lhs = fm::log(V * inv_alpha / (a / (us * us) + b));
+    if (lhs <= log_pois_pmf(k, lam)) return k;
+  }
+  cx.err |= kErrSamplerCap;
+  return (int32_t)floorf(lam);
+}
+
+EN_D int32_t binomial_half(int32_t n, float p, PhiloxStream& st, SamplerCtx& cx) {
+  const float nf = (float)n;
+  const float np = nf * p;
+  const float q = 1.0f - p;
+  if (np < 10.0f) {
+    const float r = p / q;
+    float pk = fm::exp(nf * fm::log1p(-p));
+    float F = pk;
+    const float u = st.uniform();
+    int32_t k = 0;
+    while (u > F) {
+      if (k == n || k == 63) break;
+      pk = ((pk * (float)(n - k)) * r) * cx.rinv[k + 1];
+      k = k + 1;
+      const float Fn = F + pk;
+      if (Fn == F) break;
+      F = Fn;
+    }
+    return k;
+  }
+  const float spq = sqrtf(np * q);
+  const float b = 1.15f + 2.53f * spq;
+  const float a = -0.0873f + 0.0248f * b + 0.01f * p;
+  const float c = np + 0.5f;
+  const float vr = 0.92f - 4.2f / b;
+  const float alpha = (2.83f + 5.1f / b) * spq;
+  int32_t mode = (int32_t)floorf((nf + 1.0f) * p);
+  if (mode > n) mode = n;
+  const float lpm = log_binom_pmf(mode, n, p, q);
+  for (int it = 0; it < cx.cap; ++it) {
+    const float u = st.uniform() - 0.5f;
+    const float v = st.uniform();
+    const float us = 0.5f - fabsf(u);
+    const float kf = floorf((2.0f * a / us + b) * u + c);
+    if (kf < 0.0f || kf > nf) continue;
+    const int32_t k = (int32_t)kf;
+    if (us >= 0.07f && v <= vr) return k;
+    const float lv = fm::log(v * alpha / (a / (us * us) + b));
+    if (lv <= log_binom_pmf(k, n, p, q) - lpm) return k;
+  }
+  cx.err |= kErrSamplerCap;
+  return (int32_t)floorf(np);
+}
+
+EN_D int32_t binomial(int32_t n, float p, PhiloxStream& st, SamplerCtx& cx) {
+  if (n <= 0 || !(p > 0.0f)) return 0;  // Appendix A: zero if the count is zero
+  if (p >= 1.0f) return n;
+  if (p > 0.5f) return n - binomial_half(n, 1.0f - p, st, cx);
+  return binomial_half(n, p, st, cx);
+}
+
+EN_D float std_normal(PhiloxStream& st, SamplerCtx& cx) {
+  for (int it = 0; it < cx.cap; ++it) {
+    const float v1 = 2.0f * st.uniform() - 1.0f;
+    const float v2 = 2.0f * st.uniform() - 1.0f;
+    const float s = v1 * v1 + v2 * v2;
+    if (s < 1.0f) {
+      const float t = (-2.0f * fm::log(s)) / s;
+      return v1 * sqrtf(t);
+    }
+  }
+  cx.err |= kErrSamplerCap;
+  return 0.0f;
+}
+
+EN_D float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
+  if (k <= 0) return 0.0f;
+  if (k <= 8) {
+    float S = 0.0f;
+    int32_t rem = k;
+    while (rem > 0) {
+      const int32_t g = rem < 4 ? rem : 4;
+      float prod = st.uniform();
+      for (int32_t j = 1; j < g; ++j) prod = prod * st.uniform();
+      S = S - fm::log(prod);
+      rem = rem - g;
+    }
+    return S / rate;
+  }
+  const float d = (float)k - (float)(1.0 / 3.0);
+  const float cc = 1.0f / sqrtf(9.0f * d);
+  for (int it = 0; it < cx.cap; ++it) {
+    const float x = std_normal(st, cx);
+    float v = 1.0f + cc * x;
+    if (v <= 0.0f) continue;
+    v = v * v * v;
+    const float u = st.uniform();
+    const float x2 = x * x;
+    if (u < 1.0f - 0.0331f * (x2 * x2)) return d * v / rate;
+    if (fm::log(u) < 0.5f * x2 + d * ((1.0f - v) + fm::log(v))) return d * v / rate;
+  }
+  cx.err |= kErrSamplerCap;
+  return (float)k / rate;
+}
+
+// GenerateDeparture(x, m, mu, h), Lemma 1 / Algorithm 1; p0 = 1 - e^{-mu h}.
+EN_D int32_t generate_departure(int32_t x, int32_t m, float mu, float h, float p0,
+                                PhiloxStream& st, SamplerCtx& cx) {
+  if (x <= m) return binomial(x, p0, st, cx);
+  const float rate = (float)m * mu;
+  const float T = erlang(x - m, rate, st, cx);
+  if (T > h) return binomial(x - m - 1, h / T, st, cx);
+  const float p = -fm::expm1(-(mu * (h - T)));
+  return (x - m) + binomial(m, p, st, cx);
+}
+
+}  // namespace eulernet
