@@ -126,6 +126,31 @@ EULERNET_API int euler_net_simulate_host(euler_net* net, int32_t scheme, double 
                             int64_t replications, uint64_t seed, int64_t rep_begin,
                             int64_t* stats_host, void* cuda_stream);
 
+/* Same computation and results as euler_net_simulate, for callers that
+ * cannot allocate device memory while they run (an application with a
+ * device-memory budget fixed at start-up, a plug-in whose host owns the
+ * allocator, a latency-critical loop where a cudaMalloc/cudaFree, which may
+ * synchronise the device, is not acceptable).  The paper has no counterpart:
+ * this is a deployment variant of the same step.
+ *
+ * It allocates nothing: its scratch (replication state, routed counts,
+ * partial sums, per-step tables) lives in one 64 MiB area that the library
+ * reserves on every GPU that loads it, held until the process exits.  The
+ * handle must have been created beforehand (creation allocates) on the
+ * current device, and `stats` is the caller's device buffer as for
+ * euler_net_simulate.  The first call on a device also looks up the scratch
+ * address for that device; make that first call before any stream capture.
+ * Runs that need more than 64 MiB of scratch (about 4(n+E)R bytes plus 32R
+ * plus 4K per external station) return EULER_ERR_TOO_LARGE.  All calls
+ * share the scratch and it keeps the previous call's contents: the call
+ * resets what must start at zero, and calls that overlap on the GPU (other
+ * streams, other threads) race and must not be issued.  Asynchronous on
+ * cuda_stream except for staging the per-step tables; device-side errors are
+ * returned by euler_net_status. */
+EULERNET_API int euler_net_simulate_noalloc(euler_net* net, int32_t scheme, double dt, double T,
+                                            int64_t replications, uint64_t seed, int64_t rep_begin,
+                                            int64_t* stats, void* cuda_stream);
+
 /* Synchronise `cuda_stream`, then return and clear the latched device-side
  * status of the handle's previous calls (EULER_OK if none failed). */
 EULERNET_API int euler_net_status(euler_net* net, void* cuda_stream);

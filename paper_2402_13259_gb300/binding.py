@@ -67,6 +67,8 @@ def lib():
         L.euler_stats_len.restype = i64
         L.euler_num_steps.argtypes = [dbl, dbl]
         L.euler_num_steps.restype = i64
+        L.euler_net_simulate_noalloc.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp]
+        L.euler_net_simulate_noalloc.restype = C.c_int
         L.euler_net_h2d_bytes.argtypes = [vp]
         L.euler_net_h2d_bytes.restype = i64
         L.euler_net_destroy.argtypes = [vp]

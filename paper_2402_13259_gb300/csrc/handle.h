@@ -1,0 +1,71 @@
+// handle.h -- the library's network handle (private; shared by the host
+// translation units, not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/eulernet.h"
+#include "internal.h"
+
+struct euler_net {
+  int32_t n = 0, E = 0, L = 0, max_level = 0, n_ex = 0;
+  std::vector<int32_t> row_ptr, col, servers, lvl_ptr, lvl_station, ex_col, N0;
+  std::vector<double> prob, mu;
+  int32_t arr_kind = EULER_ARR_NONE;
+  std::vector<double> w, table;
+  double a = 0, b = 0, period = 1, phase = 0, tab_dt = 1;
+  int32_t table_len = 0;
+
+  int device = 0, sm_count = 0, smem_optin = 0;
+  int32_t *d_lvl_ptr = nullptr, *d_lvl_station = nullptr, *d_row_ptr = nullptr, *d_in_ptr = nullptr,
+          *d_in_edge = nullptr, *d_servers = nullptr, *d_N0 = nullptr, *d_ex_col = nullptr;
+  float *d_qc = nullptr, *d_mu = nullptr;
+  unsigned* d_err = nullptr;
+
+  // per-(dt, T) tables of the last call
+  double c_dt = -1.0, c_T = -1.0;
+  int32_t c_K = 0;
+  float* d_p0 = nullptr;
+  float* d_lam = nullptr;
+  size_t lam_cap = 0;
+
+  // HBM-form state
+  int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr;
+  int64_t* d_racc = nullptr;
+  int64_t hbm_cap_ld = 0, hbm_cap_R = 0;
+  cudaStream_t cap_stream = nullptr;
+
+  int64_t opt[6] = {-1, -1, -1, -1, -1, -1};
+  int64_t h2d_bytes = 0;  // host-to-device bytes copied by this handle so far
+
+  eulernet::NetTables tables() const {
+    eulernet::NetTables t;
+    t.n = n;
+    t.E = E;
+    t.L = L;
+    t.max_level = max_level;
+    t.lvl_ptr = d_lvl_ptr;
+    t.lvl_station = d_lvl_station;
+    t.row_ptr = d_row_ptr;
+    t.qc = d_qc;
+    t.in_ptr = d_in_ptr;
+    t.in_edge = d_in_edge;
+    t.servers = d_servers;
+    t.mu = d_mu;
+    t.N0 = N0.empty() ? nullptr : d_N0;
+    t.ex_col = d_ex_col;
+    t.n_ex = n_ex;
+    return t;
+  }
+};
+
+namespace eulernet {
+// Per-step mean of the external arrivals of station i over step tau: the
+// exact integral of lambda_i over ((tau-1) dt, tau dt] (Sec. 2.1.1), in double.
+double step_mean(const euler_net& h, int32_t i, int64_t tau, double dt);
+// Set the message euler_net_last_error() returns on this thread.
+void set_last_error(const char* msg);
+}  // namespace eulernet

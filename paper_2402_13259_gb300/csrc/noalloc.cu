@@ -1,0 +1,184 @@
+// noalloc.cu -- euler_net_simulate_noalloc: the HBM-state form of the Euler
+// step run entirely out of a fixed scratch area that the library reserves
+// when it is loaded, so the call itself allocates no device memory.
+//
+// Who needs it: programs that cannot call cudaMalloc/cudaFree while they run
+// -- a host application with a device-memory budget fixed at start-up, a
+// plug-in whose host owns the device allocator, or a latency-critical loop in
+// which an allocation (which may synchronise the device) is not acceptable.
+// They create the network handle once during set-up and then call this entry
+// point; it writes into their own stats buffer.
+//
+// The scratch is one file-scope __device__ array (kScratchBytes, 64 MiB).
+// Every GPU that loads this library holds it until the process exits.  All
+// calls share it and it keeps the previous call's contents, so this file
+// clears what must start at zero on every call, and calls that overlap on the
+// GPU (on different streams, or from different threads) race on it.
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "handle.h"
+#include "internal.h"
+#include "sampling.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(64) << 20;
+constexpr int kMaxDevices = 64;
+
+// The reserved scratch.  In host code this name is only a host-side stand-in
+// for the device symbol: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_setup_mutex;
+void* g_scratch_addr[kMaxDevices];  // device address of g_scratch, per device
+
+// Resolve the scratch's device address once per device, with that device
+// current.  The first call of the entry point on a device does this set-up.
+cudaError_t scratch_address(int device, unsigned char** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+  return cudaSuccess;
+}
+
+__global__ void fold_error_kernel(const unsigned* src, unsigned* dst) {
+  if (*src) atomicOr(dst, *src);
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int noalloc_fail(int code, const char* msg) {
+  eulernet::set_last_error(msg);
+  return code;
+}
+
+// Host staging for the per-step tables: a fixed buffer, refilled chunk by
+// chunk (a copy from pageable memory returns once the data is staged).
+constexpr int kStage = 4096;
+thread_local float g_stage[kStage];
+
+}  // namespace
+
+extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t scheme, double dt,
+                                                       double T, int64_t R, uint64_t seed,
+                                                       int64_t rep_begin, int64_t* stats,
+                                                       void* cuda_stream) {
+  using namespace eulernet;
+  if (!h) return noalloc_fail(EULER_ERR_ARG, "handle is NULL");
+  if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return noalloc_fail(EULER_ERR_ARG, "unknown scheme");
+  if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T))
+    return noalloc_fail(EULER_ERR_ARG, "dt and T must be finite and > 0");
+  if (R < 0 || rep_begin < 0 || !stats) return noalloc_fail(EULER_ERR_ARG, "bad replications, rep_begin or stats");
+  if (rep_begin + R > (int64_t)1 << 32) return noalloc_fail(EULER_ERR_TOO_LARGE, "replication index beyond 2^32");
+  const int64_t K = euler_num_steps(dt, T);
+  if (K >= (1 << 24)) return noalloc_fail(EULER_ERR_TOO_LARGE, "too many steps (T/dt >= 2^24)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+
+  // scratch layout: [err, tau] | p0[n] | lam[K][n_ex] | racc[R][4] | N[n][ld] | Redge[E][ld]
+  const int64_t ld = (R + 3) / 4 * 4;
+  const int64_t n_ex = h->n_ex > 0 ? h->n_ex : 1;
+  size_t off = 256;
+  const size_t off_p0 = off;
+  off = align256(off + sizeof(float) * (size_t)h->n);
+  const size_t off_lam = off;
+  off = align256(off + sizeof(float) * (size_t)K * (size_t)n_ex);
+  const size_t off_racc = off;
+  off = align256(off + sizeof(int64_t) * 4 * (size_t)(R > 0 ? R : 1));
+  const size_t off_N = off;
+  off = align256(off + sizeof(int32_t) * (size_t)h->n * (size_t)ld);
+  const size_t off_Redge = off;
+  off = align256(off + sizeof(int32_t) * (size_t)(h->E > 0 ? h->E : 1) * (size_t)ld);
+  if (off > kScratchBytes)
+    return noalloc_fail(EULER_ERR_TOO_LARGE,
+                        "this run needs more scratch than the 64 MiB the no-allocation entry point "
+                        "reserves (n*R + E*R int32 state, 32 B per replication, the per-step tables)");
+
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  unsigned char* base = nullptr;
+  if (e == cudaSuccess) e = scratch_address(device, &base);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s);
+  if (e != cudaSuccess) return noalloc_fail(EULER_ERR_CUDA, cudaGetErrorString(e));
+  if (R == 0) return EULER_OK;
+
+  // per-call tables, computed as euler_net_simulate computes them
+  float* d_p0 = reinterpret_cast<float*>(base + off_p0);
+  float* d_lam = reinterpret_cast<float*>(base + off_lam);
+  for (int32_t i0 = 0; i0 < h->n && e == cudaSuccess; i0 += kStage) {
+    const int32_t cnt = h->n - i0 < kStage ? h->n - i0 : kStage;
+    for (int32_t k = 0; k < cnt; ++k) {
+      const float y = (float)(h->mu[i0 + k] * dt);
+      g_stage[k] = -fm::expm1(-y);
+    }
+    e = cudaMemcpyAsync(d_p0 + i0, g_stage, sizeof(float) * cnt, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // staging buffer is reused
+  }
+  if (h->n_ex > 0) {
+    const int64_t total = K * h->n_ex;
+    for (int64_t j0 = 0; j0 < total && e == cudaSuccess; j0 += kStage) {
+      const int64_t cnt = total - j0 < kStage ? total - j0 : kStage;
+      for (int64_t k = 0; k < cnt; ++k) g_stage[k] = 0.0f;
+      for (int32_t i = 0; i < h->n; ++i) {
+        const int32_t c = h->ex_col[i];
+        if (c < 0) continue;
+        // entries j = (tau-1)*n_ex + c inside [j0, j0+cnt)
+        int64_t tau0 = (j0 - c + h->n_ex - 1) / h->n_ex + 1;
+        if (tau0 < 1) tau0 = 1;
+        for (int64_t tau = tau0; tau <= K; ++tau) {
+          const int64_t j = (tau - 1) * h->n_ex + c;
+          if (j >= j0 + cnt) break;
+          if (j >= j0) g_stage[j - j0] = (float)step_mean(*h, i, tau, dt);
+        }
+      }
+      e = cudaMemcpyAsync(d_lam + j0, g_stage, sizeof(float) * (size_t)cnt, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // staging buffer is reused
+    }
+  }
+  unsigned* d_err = reinterpret_cast<unsigned*>(base);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return noalloc_fail(EULER_ERR_CUDA, cudaGetErrorString(e));
+
+  RunParams p;
+  p.p0 = d_p0;
+  p.lam = d_lam;
+  p.h = (float)dt;
+  p.K = (int32_t)K;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.R = R;
+  p.rep_begin = rep_begin;
+  p.scheme = scheme;
+  p.tile_reps = 32;
+  p.num_tiles = (R + 31) / 32;
+  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+  p.stats = stats;
+  p.err = d_err;
+  HbmState hs;
+  hs.tau = reinterpret_cast<int32_t*>(base + 4);
+  hs.racc = reinterpret_cast<int64_t*>(base + off_racc);
+  hs.N = reinterpret_cast<int32_t*>(base + off_N);
+  hs.Redge = reinterpret_cast<int32_t*>(base + off_Redge);
+  hs.ld = ld;
+  const NetTables t = h->tables();
+  e = launch_hbm_init(t, p, hs, s);  // N = N0, partial sums = 0, tau = 1
+  for (int64_t k = 0; k < K && e == cudaSuccess; ++k)
+    e = launch_hbm_step(t, p, hs, 256, h->lvl_ptr.data(), s);
+  if (e == cudaSuccess) e = launch_hbm_finish(t, p, hs, s);
+  if (e == cudaSuccess) {
+    fold_error_kernel<<<1, 1, 0, s>>>(d_err, h->d_err);  // report through euler_net_status
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return noalloc_fail(EULER_ERR_CUDA, cudaGetErrorString(e));
+  return EULER_OK;
+}
