@@ -193,7 +193,8 @@ def main():
     run = workload()
     K = Bd.num_steps(run.dt, run.T)
     n, R = run.net.n, run.R
-    rep_begin = rank * R
+    from paper_2402_13259_gb300 import sharding
+    rep_begin, R = sharding.replica_range(rank, world, R, "weak")
     units_per_step = 2 * n * K * R  # per rank
     h = Bd.EulerNet(run.net)
     stream = torch.cuda.current_stream()

@@ -48,7 +48,8 @@ enum {
   EULER_ERR_OOM = -4,             /* device allocation failed                     */
   EULER_ERR_SAMPLER_CAP = -5,     /* a rejection loop hit its iteration cap       */
   EULER_ERR_OVERFLOW = -6,        /* a station count exceeded 2^30                */
-  EULER_ERR_TOO_LARGE = -7        /* sizes beyond this library's index ranges     */
+  EULER_ERR_TOO_LARGE = -7,       /* sizes beyond this library's index ranges     */
+  EULER_ERR_STALL = -8            /* a bounded wait between warps timed out       */
 };
 
 enum { EULER_BACKWARD = 0, EULER_FORWARD = 1 };
@@ -158,18 +159,27 @@ EULERNET_API int euler_net_status(euler_net* net, void* cuda_stream);
 /* Tuning and testing options (see EULER_OPT_*); value < 0 restores the
  * default.  Returns EULER_OK or EULER_ERR_ARG. */
 enum {
-  EULER_OPT_FORM = 0,        /* 0 = auto, 1 = persistent shared-memory kernel,
-                                2 = per-step kernels over HBM state (graph)    */
+  EULER_OPT_FORM = 0,        /* 0 = auto, 1 = persistent shared-memory kernel
+                                with block barriers, 2 = per-step kernels over
+                                HBM state (graph), 3 = level-pipelined
+                                shared-memory kernel                           */
   EULER_OPT_TILE_REPS = 1,   /* replications per tile (power of two)           */
   EULER_OPT_BLOCK = 2,       /* threads per block                              */
   EULER_OPT_GRID = 3,        /* blocks of the persistent kernel (0 = auto)     */
   EULER_OPT_SAMPLER_CAP = 4, /* rejection-loop iteration cap (default 1000)    */
-  EULER_OPT_GRAPH_STEPS = 5  /* steps captured per CUDA graph (HBM form)       */
+  EULER_OPT_GRAPH_STEPS = 5, /* steps captured per CUDA graph (HBM form)       */
+  EULER_OPT_PIPE_WARPS = 6,  /* warps per tile of the pipelined form (<= 16)   */
+  EULER_OPT_WAIT_LIMIT = 7,  /* polls before an inter-warp wait of the
+                                pipelined form gives up (default 2^25, about
+                                2-4 s); then EULER_ERR_STALL                   */
+  EULER_OPT_TEST_STALL = 8   /* testing only: nonzero makes every warp of the
+                                pipelined form withhold its progress, so the
+                                warps' bounded waits run out                  */
 };
 EULERNET_API int euler_net_set_option(euler_net* net, int32_t option, int64_t value);
 
 /* Describe the launch the next euler_net_simulate would make for these
- * sizes: form (1 or 2), tile replications, block, grid, shared bytes.
+ * sizes: form (1, 2 or 3), tile replications, block, grid, shared bytes.
  * Host only; no device work. */
 EULERNET_API int euler_net_plan(euler_net* net, int32_t scheme, int64_t replications, int32_t* form,
                    int32_t* tile_reps, int32_t* block, int32_t* grid, int32_t* smem_bytes);

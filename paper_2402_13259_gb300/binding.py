@@ -20,11 +20,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libeulernet.so")
 
 BACKWARD, FORWARD = 0, 1
-OPT_FORM, OPT_TILE_REPS, OPT_BLOCK, OPT_GRID, OPT_SAMPLER_CAP, OPT_GRAPH_STEPS = range(6)
+(OPT_FORM, OPT_TILE_REPS, OPT_BLOCK, OPT_GRID, OPT_SAMPLER_CAP, OPT_GRAPH_STEPS, OPT_PIPE_WARPS,
+ OPT_WAIT_LIMIT, OPT_TEST_STALL) = range(9)
 
 ERRORS = {
     -1: "EULER_ERR_ARG", -2: "EULER_ERR_NOT_FEEDFORWARD", -3: "EULER_ERR_CUDA", -4: "EULER_ERR_OOM",
     -5: "EULER_ERR_SAMPLER_CAP", -6: "EULER_ERR_OVERFLOW", -7: "EULER_ERR_TOO_LARGE",
+    -8: "EULER_ERR_STALL",
 }
 
 

@@ -108,10 +108,11 @@ namespace {
 int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
   const int64_t K = euler_num_steps(dt, T);
   if (h->c_dt == dt && h->c_T == T) return EULER_OK;
-  std::vector<float> p0(h->n);
+  std::vector<float4> p0(h->n);
   for (int32_t i = 0; i < h->n; ++i) {
     const float y = (float)(h->mu[i] * dt);
-    p0[i] = -fm::expm1(-y);
+    const BinomConst bc = binom_const(-fm::expm1(-y));
+    p0[i] = make_float4(bc.c0, bc.q, bc.r, bc.lq);
   }
   std::vector<float> lam((size_t)K * std::max(h->n_ex, 1), 0.0f);
   for (int32_t i = 0; i < h->n; ++i) {
@@ -119,16 +120,16 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
     if (c < 0) continue;
     for (int64_t tau = 1; tau <= K; ++tau) lam[(size_t)(tau - 1) * h->n_ex + c] = (float)step_mean(*h, i, tau, dt);
   }
-  if (!h->d_p0) CUDA_TRY(cudaMalloc(&h->d_p0, sizeof(float) * (size_t)h->n));
+  if (!h->d_p0) CUDA_TRY(cudaMalloc(&h->d_p0, sizeof(float4) * (size_t)h->n));
   if (lam.size() > h->lam_cap) {
     if (h->d_lam) CUDA_TRY(cudaFree(h->d_lam));
     h->d_lam = nullptr;
     CUDA_TRY(cudaMalloc(&h->d_lam, sizeof(float) * lam.size()));
     h->lam_cap = lam.size();
   }
-  CUDA_TRY(cudaMemcpyAsync(h->d_p0, p0.data(), sizeof(float) * p0.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(h->d_p0, p0.data(), sizeof(float4) * p0.size(), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(h->d_lam, lam.data(), sizeof(float) * lam.size(), cudaMemcpyHostToDevice, s));
-  h->h2d_bytes += (int64_t)(sizeof(float) * (p0.size() + lam.size()));
+  h->h2d_bytes += (int64_t)(sizeof(float4) * p0.size() + sizeof(float) * lam.size());
   CUDA_TRY(cudaStreamSynchronize(s));  // host staging buffers go out of scope
   h->c_dt = dt;
   h->c_T = T;
@@ -139,7 +140,30 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
 struct Plan {
   int form = 1, tile_reps = 32, block = 32, grid = 1;
   int64_t smem = 0, num_tiles = 0;
+  PipePlan pipe;
 };
+
+// Cut the level-ordered stations into W contiguous slices and record, per
+// slice, which other slices it receives from and sends to.
+bool make_pipe_plan(const euler_net* h, int W, PipePlan* pp) {
+  const int32_t n = h->n;
+  if (W < 1 || W > 32 || W > n) return false;
+  pp->W = W;
+  for (int w = 0; w <= W; ++w) pp->wbeg[w] = (int32_t)(((int64_t)w * n) / W);
+  std::vector<int32_t> owner(n, 0);
+  for (int w = 0; w < W; ++w)
+    for (int32_t k = pp->wbeg[w]; k < pp->wbeg[w + 1]; ++k) owner[h->lvl_station[k]] = w;
+  for (int w = 0; w < 32; ++w) pp->prod[w] = pp->cons[w] = 0u;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t e = h->row_ptr[i]; e < h->row_ptr[i + 1]; ++e) {
+      const int a = owner[i], b = owner[h->col[e]];
+      if (a == b) continue;
+      if (a > b) return false;  // cannot happen for level order
+      pp->cons[a] |= 1u << b;
+      pp->prod[b] |= 1u << a;
+    }
+  return true;
+}
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -156,6 +180,30 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
         Rt = cand;
         break;
       }
+  }
+  if (forced_form == 3) {
+    const int W = h->opt[EULER_OPT_PIPE_WARPS] > 0 ? (int)h->opt[EULER_OPT_PIPE_WARPS]
+                                                   : (int)std::min<int64_t>(h->n, 16);
+    const int64_t psmem = pipeline_smem_bytes(h->n, h->E);
+    bool fits = W <= 16 && psmem <= limit && make_pipe_plan(h, W, &pl->pipe);
+    int per_sm = 0;
+    if (fits) {
+      cudaError_t e = pipeline_occupancy(scheme, 32 * W, (int)psmem, &per_sm);
+      if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+      fits = per_sm >= 1;
+    }
+    if (fits) {
+      pl->form = 3;
+      pl->tile_reps = 32;
+      pl->block = 32 * W;
+      pl->smem = psmem;
+      pl->num_tiles = (R + 31) / 32;
+      int64_t grid = (int64_t)per_sm * h->sm_count;
+      if (h->opt[EULER_OPT_GRID] > 0) grid = h->opt[EULER_OPT_GRID];
+      pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, pl->num_tiles));
+      return EULER_OK;
+    }
+    if (forced_form == 3) return fail(EULER_ERR_TOO_LARGE, "pipelined form does not fit");
   }
   pl->form = (forced_form == 1 || forced_form == 2) ? forced_form : 1;
   if (pl->form == 1 && (Rt < 1 || persistent_smem_bytes(h->n, h->E, Rt) > limit)) {
@@ -190,7 +238,7 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   pl->smem = persistent_smem_bytes(h->n, h->E, Rt);
   pl->num_tiles = (R + Rt - 1) / Rt;
   int per_sm = 0;
-  cudaError_t e = persistent_occupancy(block, (int)pl->smem, &per_sm);
+  cudaError_t e = persistent_occupancy(scheme, block, (int)pl->smem, &per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   if (per_sm < 1) {
     if (forced_form == 1) return fail(EULER_ERR_TOO_LARGE, "persistent kernel cannot be resident");
@@ -398,7 +446,7 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
   for (int32_t j = 0; j < h->L; ++j) h->max_level = std::max(h->max_level, h->lvl_ptr[j + 1] - h->lvl_ptr[j]);
 
   // conditional split probabilities qc_e = p_e / (p_exit + sum_{e' >= e} p_e')
-  std::vector<float> qc(std::max(h->E, 1), 0.0f);
+  std::vector<float> qc(std::max(h->E, 1), 0.0f);  // conditional split probabilities
   for (int32_t i = 0; i < n; ++i) {
     const int32_t e0 = h->row_ptr[i], e1 = h->row_ptr[i + 1];
     double rowsum = 0.0;
@@ -431,6 +479,11 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
       for (int32_t j = 0; j < h->table_len && !ext; ++j) ext = h->table[(int64_t)j * n + i] != 0.0;
     if (ext) h->ex_col[i] = h->n_ex++;
   }
+  std::vector<float4> qc_const(qc.size());
+  for (size_t e = 0; e < qc.size(); ++e) {
+    const BinomConst bc = binom_const(qc[e]);
+    qc_const[e] = make_float4(bc.c0, bc.q, bc.r, bc.lq);
+  }
   std::vector<float> mu_f(n);
   for (int32_t i = 0; i < n; ++i) mu_f[i] = (float)h->mu[i];
 
@@ -446,7 +499,7 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
   if (e == cudaSuccess) e = upload(&h->d_servers, h->servers, &h->h2d_bytes);
   if (e == cudaSuccess) e = upload(&h->d_N0, h->N0, &h->h2d_bytes);
   if (e == cudaSuccess) e = upload(&h->d_ex_col, h->ex_col, &h->h2d_bytes);
-  if (e == cudaSuccess) e = upload(&h->d_qc, qc, &h->h2d_bytes);
+  if (e == cudaSuccess) e = upload(&h->d_qc, qc_const, &h->h2d_bytes);
   if (e == cudaSuccess) e = upload(&h->d_mu, mu_f, &h->h2d_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(unsigned));
@@ -461,7 +514,7 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
 int64_t euler_net_h2d_bytes(const euler_net* h) { return h ? h->h2d_bytes : -1; }
 
 int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
-  if (!h || option < 0 || option > EULER_OPT_GRAPH_STEPS) return fail(EULER_ERR_ARG, "bad option");
+  if (!h || option < 0 || option > EULER_OPT_TEST_STALL) return fail(EULER_ERR_ARG, "bad option");
   h->opt[option] = value < 0 ? -1 : value;
   return EULER_OK;
 }
@@ -513,7 +566,14 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
   p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
   p.stats = stats;
   p.err = h->d_err;
+  p.wait_limit = h->opt[EULER_OPT_WAIT_LIMIT] > 0 ? h->opt[EULER_OPT_WAIT_LIMIT] : (int64_t)1 << 25;
+  p.test_stall = h->opt[EULER_OPT_TEST_STALL] > 0 ? 1 : 0;
   const NetTables t = h->tables();
+  if (pl.form == 3) {
+    cudaError_t e = launch_pipeline(t, p, pl.pipe, pl.grid, (int)pl.smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pipelined kernel launch");
+    return EULER_OK;
+  }
   if (pl.form == 1) {
     cudaError_t e = launch_persistent(t, p, pl.grid, pl.block, (int)pl.smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
@@ -531,6 +591,7 @@ int euler_net_status(euler_net* h, void* stream) {
   CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(unsigned)));
   if (bits & kErrSamplerCap) return fail(EULER_ERR_SAMPLER_CAP, "a sampler rejection loop hit its cap");
   if (bits & kErrOverflow) return fail(EULER_ERR_OVERFLOW, "a station count exceeded 2^30");
+  if (bits & kErrStall) return fail(EULER_ERR_STALL, "a wait between warps of the pipelined kernel timed out");
   return EULER_OK;
 }
 

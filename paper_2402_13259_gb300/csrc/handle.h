@@ -22,13 +22,14 @@ struct euler_net {
   int device = 0, sm_count = 0, smem_optin = 0;
   int32_t *d_lvl_ptr = nullptr, *d_lvl_station = nullptr, *d_row_ptr = nullptr, *d_in_ptr = nullptr,
           *d_in_edge = nullptr, *d_servers = nullptr, *d_N0 = nullptr, *d_ex_col = nullptr;
-  float *d_qc = nullptr, *d_mu = nullptr;
+  float4* d_qc = nullptr;
+  float* d_mu = nullptr;
   unsigned* d_err = nullptr;
 
   // per-(dt, T) tables of the last call
   double c_dt = -1.0, c_T = -1.0;
   int32_t c_K = 0;
-  float* d_p0 = nullptr;
+  float4* d_p0 = nullptr;
   float* d_lam = nullptr;
   size_t lam_cap = 0;
 
@@ -38,7 +39,7 @@ struct euler_net {
   int64_t hbm_cap_ld = 0, hbm_cap_R = 0;
   cudaStream_t cap_stream = nullptr;
 
-  int64_t opt[6] = {-1, -1, -1, -1, -1, -1};
+  int64_t opt[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
   int64_t h2d_bytes = 0;  // host-to-device bytes copied by this handle so far
 
   eulernet::NetTables tables() const {

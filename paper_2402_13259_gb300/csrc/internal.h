@@ -17,7 +17,7 @@ struct NetTables {
   const int32_t* lvl_ptr;      // [L+1] offsets into lvl_station
   const int32_t* lvl_station;  // [n] stations ordered by (level, index)
   const int32_t* row_ptr;      // [n+1] CSR (routing P)
-  const float* qc;             // [E] conditional split probability of each edge
+  const float4* qc;            // [E] BinomConst of each edge's conditional split probability
   const int32_t* in_ptr;       // [n+1] CSC offsets (edges into each station)
   const int32_t* in_edge;      // [E] edge ids into each station
   const int32_t* servers;      // [n] m_i
@@ -29,7 +29,7 @@ struct NetTables {
 
 // Per-call parameters.
 struct RunParams {
-  const float* p0;   // [n] 1 - e^{-mu_i dt}
+  const float4* p0;  // [n] BinomConst of 1 - e^{-mu_i dt}
   const float* lam;  // [K][n_ex] per-step arrival means
   float h;           // dt rounded to float
   int32_t K;         // steps
@@ -40,6 +40,8 @@ struct RunParams {
   int32_t tile_reps;  // replications per tile (power of two)
   int64_t num_tiles;
   int32_t cap;        // rejection-loop cap
+  int64_t wait_limit; // polls of one inter-warp wait before it gives up (pipelined form)
+  int32_t test_stall; // nonzero: no warp publishes progress (tests the timeout path)
   int64_t* stats;     // output, see eulernet.h
   unsigned* err;      // latched error bits
 };
@@ -52,7 +54,22 @@ cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, 
                               int smem, cudaStream_t s);
 
 // Blocks of `block` threads with `smem` bytes that fit on one SM.
-cudaError_t persistent_occupancy(int block, int smem, int* blocks_per_sm);
+cudaError_t persistent_occupancy(int scheme, int block, int smem, int* blocks_per_sm);
+
+// Level-pipelined form: W warps per 32-replication tile, warp w owns the
+// level-ordered station slice lvl_station[wbeg[w] .. wbeg[w+1]); prod[w] and
+// cons[w] are the bit masks of the warps it receives routed customers from and
+// sends them to.
+struct PipePlan {
+  int32_t W;
+  int32_t wbeg[33];
+  uint32_t prod[32];
+  uint32_t cons[32];
+};
+int64_t pipeline_smem_bytes(int32_t n, int32_t E);
+cudaError_t pipeline_occupancy(int scheme, int block, int smem, int* blocks_per_sm);
+cudaError_t launch_pipeline(const NetTables& t, const RunParams& p, const PipePlan& pp, int grid,
+                            int smem, cudaStream_t s);
 
 // HBM-state form: per-step kernels over state in global memory.
 struct HbmState {

@@ -23,167 +23,18 @@
 
 #include "internal.h"
 #include "sampling.cuh"
+#include "unit.cuh"
 
 namespace eulernet {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ void latch(unsigned* err, unsigned bits) {
-  if (bits) atomicOr(err, bits);
-}
-
-// Sequential conditional binomials along the CSR row (Sec. 2.2 multinomial).
-__device__ __forceinline__ int32_t route_row(int32_t D, int32_t e0, int32_t e1, const float* qc,
-                                             int32_t* redge, int64_t stride, int64_t col,
-                                             PhiloxStream& st, SamplerCtx& cx) {
-  int32_t rem = D;
-  for (int32_t e = e0; e < e1; ++e) {
-    int32_t v = 0;
-    if (rem > 0) v = binomial(rem, __ldg(qc + e), st, cx);
-    redge[(int64_t)e * stride + col] = v;
-    rem = rem - v;
-  }
-  return rem;
-}
-
-__device__ __forceinline__ int64_t gather_in(const NetTables& t, int32_t i, const int32_t* redge,
-                                             int64_t stride, int64_t col) {
-  int64_t s = 0;
-  const int32_t k1 = __ldg(t.in_ptr + i + 1);
-  for (int32_t k = __ldg(t.in_ptr + i); k < k1; ++k)
-    s += redge[(int64_t)__ldg(t.in_edge + k) * stride + col];
-  return s;
-}
-
-// Sum `v` over aligned segments of `w` lanes (w a power of two <= 32); the
-// segment total ends up in every lane of the segment.
-__device__ __forceinline__ unsigned seg_sum32(unsigned v, int w) {
-  if (w == 32) return __reduce_add_sync(kFull, v);
-  for (int off = w >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-  return v;
-}
-
-__device__ __forceinline__ long long seg_sum64(long long v, int w) {
-  for (int off = w >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-  return v;
-}
-
-// Reduce NV per-unit values over the replication segment and add them to
-// dst[0..NV) by the segment leader.  `fits` must be warp-uniform-safe: it is
-// combined with __all_sync here.  mode 0: plain add (exclusive owner), 1:
-// shared/global atomic add.
-template <int NV>
-__device__ __forceinline__ void reduce_to(long long* dst, const int32_t (&v)[NV], bool lead,
-                                          int w, bool atomic) {
-  int32_t vmax = 0;
-#pragma unroll
-  for (int s = 0; s < NV; ++s) vmax = v[s] > vmax ? v[s] : vmax;
-  const bool small = __all_sync(kFull, vmax < (1 << 27));
-  long long tot[NV];
-  if (small) {
-#pragma unroll
-    for (int s = 0; s < NV; ++s) tot[s] = (long long)seg_sum32((unsigned)v[s], w);
-  } else {
-#pragma unroll
-    for (int s = 0; s < NV; ++s) tot[s] = seg_sum64((long long)v[s], w);
-  }
-  if (lead) {
-#pragma unroll
-    for (int s = 0; s < NV; ++s) {
-      if (atomic)
-        atomicAdd(reinterpret_cast<unsigned long long*>(dst + s), (unsigned long long)tot[s]);
-      else
-        dst[s] += tot[s];
-    }
-  }
-}
-
-// ---- one unit of each scheme -------------------------------------------------
-
-struct UnitOut {
-  int32_t N, D, X, A;
-};
-
-// Backward phase 1 at station i: D from N_{tau-1}, routing, external arrivals;
-// stores N_{tau-1} - D + A^ex (the gather is added in phase 2).
-__device__ __forceinline__ UnitOut backward_departures(const NetTables& t, const RunParams& p,
-                                                       int32_t i, uint32_t tau, uint32_t rep,
-                                                       const float* lam_t, int32_t* nstate,
-                                                       int32_t* redge, int64_t stride,
-                                                       int64_t col, SamplerCtx& cx) {
-  UnitOut o;
-  const int32_t x = nstate[(int64_t)i * stride + col];
-  PhiloxStream svc;
-  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
-  o.D = generate_departure(x, __ldg(t.servers + i), __ldg(t.mu + i), p.h, __ldg(p.p0 + i), svc, cx);
-  o.X = route_row(o.D, __ldg(t.row_ptr + i), __ldg(t.row_ptr + i + 1), t.qc, redge, stride, col, svc,
-                  cx);
-  o.A = 0;
-  const int32_t ec = __ldg(t.ex_col + i);
-  if (ec >= 0) {
-    PhiloxStream arr;
-    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
-    o.A = poisson(__ldg(lam_t + ec), arr, cx);
-  }
-  long long part = (long long)x - o.D + o.A;
-  if (part > 0x7fffffffLL) part = 0x7fffffffLL;
-  nstate[(int64_t)i * stride + col] = (int32_t)part;
-  o.N = 0;
-  return o;
-}
-
-// Backward phase 2: N_tau = (N_{tau-1} - D + A^ex) + A^in.
-__device__ __forceinline__ int32_t backward_gather(const NetTables& t, int32_t i, int32_t* nstate,
-                                                   const int32_t* redge, int64_t stride,
-                                                   int64_t col, unsigned& err) {
-  long long nn = (long long)nstate[(int64_t)i * stride + col] + gather_in(t, i, redge, stride, col);
-  if (nn > kStateLimit) {
-    err |= kErrOverflow;
-    nn = kStateLimit;
-  }
-  nstate[(int64_t)i * stride + col] = (int32_t)nn;
-  return (int32_t)nn;
-}
-
-// Forward unit at station i (its upstream stations are already done).
-__device__ __forceinline__ UnitOut forward_unit(const NetTables& t, const RunParams& p, int32_t i,
-                                                uint32_t tau, uint32_t rep, const float* lam_t,
-                                                int32_t* nstate, int32_t* redge, int64_t stride,
-                                                int64_t col, SamplerCtx& cx) {
-  UnitOut o;
-  o.A = 0;
-  const int32_t ec = __ldg(t.ex_col + i);
-  if (ec >= 0) {
-    PhiloxStream arr;
-    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
-    o.A = poisson(__ldg(lam_t + ec), arr, cx);
-  }
-  long long y = (long long)nstate[(int64_t)i * stride + col] + o.A + gather_in(t, i, redge, stride, col);
-  if (y > kStateLimit) {
-    cx.err |= kErrOverflow;
-    y = kStateLimit;
-  }
-  PhiloxStream svc;
-  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
-  o.D = generate_departure((int32_t)y, __ldg(t.servers + i), __ldg(t.mu + i), p.h, __ldg(p.p0 + i),
-                           svc, cx);
-  o.N = (int32_t)y - o.D;
-  nstate[(int64_t)i * stride + col] = o.N;
-  o.X = route_row(o.D, __ldg(t.row_ptr + i), __ldg(t.row_ptr + i + 1), t.qc, redge, stride, col, svc,
-                  cx);
-  return o;
-}
-
-__device__ __forceinline__ void fill_rinv(float* rinv) {
-  for (int k = threadIdx.x; k < 64; k += blockDim.x) rinv[k] = k ? 1.0f / (float)k : 0.0f;
-}
-
 // ---- persistent shared-memory kernel -----------------------------------------
 
 // Shared layout: rinv[64] f32 | sacc[n][6] i64 | racc[Rt][4] i64 | N[n][Rt] i32 | Redge[E][Rt] i32
-__global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams p) {
+// SCHEME 0 = backward, 1 = forward.
+template <int SCHEME>
+__global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int32_t n = t.n;
   const int Rt = p.tile_reps;
@@ -203,6 +54,12 @@ __global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams 
   const bool lead = (lane & (w - 1)) == 0;
   const bool shared_station = Rt > 32;  // several warps per station -> atomics
 
+  // With one warp per station-unit (Rt = 32) warps claim the stations of a
+  // phase dynamically; claim[phase parity] counts the stations handed out.
+  __shared__ int claim[2];
+  const bool dynamic = Rt == 32;
+  int phase = 0;
+
   fill_rinv(rinv);
   for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sacc[k] = 0;
   SamplerCtx cx{rinv, p.cap, 0u};
@@ -215,18 +72,35 @@ __global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams 
     for (int64_t k = tid; k < (int64_t)n * Rt; k += nthr)
       Ns[k] = t.N0 ? __ldg(t.N0 + k / Rt) : 0;
     for (int k = tid; k < 4 * Rt; k += nthr) racc[k] = 0;
+    if (tid < 2) claim[tid] = 0;
+    phase = 0;
     long long q_r = 0, d_r = 0, x_r = 0, a_r = 0;
     __syncthreads();
 
+    // next station slot of this warp in the current phase (m slots)
+    auto next_slot = [&](int su0, int m) -> int {
+      if (!dynamic) return su0 + G;
+      int s = 0;
+      if (lane == 0) s = atomicAdd(&claim[phase & 1], 1);
+      return __shfl_sync(kFull, s, 0);
+    };
+    auto first_slot = [&]() -> int {
+      if (!dynamic) return gwarp;
+      if (tid == 0) claim[(phase + 1) & 1] = 0;  // counter of the next phase
+      int s = 0;
+      if (lane == 0) s = atomicAdd(&claim[phase & 1], 1);
+      return __shfl_sync(kFull, s, 0);
+    };
+
     for (int32_t tau = 1; tau <= p.K; ++tau) {
       const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
-      if (p.scheme == 0) {
-        for (int su0 = gwarp; su0 < n; su0 += G) {
+      if (SCHEME == 0) {
+        for (int su0 = first_slot(); su0 < n; su0 = next_slot(su0, n)) {
           const int su = su0 + (g0 - gwarp);
           const bool act = rvalid && su < n;
           int32_t v[3] = {0, 0, 0};
           if (act) {
-            UnitOut o = backward_departures(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+            const UnitOut o = unit_update<false>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
             v[0] = o.D;
             v[1] = o.X;
             v[2] = o.A;
@@ -237,8 +111,9 @@ __global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams 
           reduce_to<3>(sacc + 6 * (int64_t)(su < n ? su : 0) + 2, v, lead && su < n, w,
                        shared_station);
         }
+        ++phase;
         __syncthreads();
-        for (int su0 = gwarp; su0 < n; su0 += G) {
+        for (int su0 = first_slot(); su0 < n; su0 = next_slot(su0, n)) {
           const int su = su0 + (g0 - gwarp);
           const bool act = rvalid && su < n;
           int32_t v[2] = {0, 0};
@@ -251,18 +126,19 @@ __global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams 
           }
           reduce_to<2>(sacc + 6 * (int64_t)(su < n ? su : 0), v, lead && su < n, w, shared_station);
         }
+        ++phase;
         __syncthreads();
       } else {
         for (int32_t j = 0; j < t.L; ++j) {
           const int32_t s0 = __ldg(t.lvl_ptr + j);
           const int32_t m = __ldg(t.lvl_ptr + j + 1) - s0;
-          for (int su0 = gwarp; su0 < m; su0 += G) {
+          for (int su0 = first_slot(); su0 < m; su0 = next_slot(su0, m)) {
             const int su = su0 + (g0 - gwarp);
             const bool act = rvalid && su < m;
             const int32_t i = su < m ? __ldg(t.lvl_station + s0 + su) : 0;
             int32_t v[5] = {0, 0, 0, 0, 0};
             if (act) {
-              UnitOut o = forward_unit(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+              const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
               const int32_t c = __ldg(t.servers + i);
               v[0] = o.N;
               v[1] = o.N < c ? o.N : c;
@@ -276,6 +152,7 @@ __global__ void __launch_bounds__(512) persistent_kernel(NetTables t, RunParams 
             }
             reduce_to<5>(sacc + 6 * (int64_t)i, v, lead && su < m, w, shared_station);
           }
+          ++phase;
           __syncthreads();
         }
       }
@@ -321,8 +198,10 @@ constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
 
 // Units of one phase over stations lvl_station[s0 .. s0+m) (or 0..n when
 // all == true).  Grid: x over replication tiles of 32, y over station chunks.
-__global__ void __launch_bounds__(256) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
-                                                        int32_t phase, int32_t s0, int32_t m) {
+template <int PHASE>
+__global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
+                                                           int32_t s0, int32_t m) {
+  constexpr int phase = PHASE;
   __shared__ float rinv[64];
   __shared__ long long racc_s[kHbmTile * 4];
   const int32_t tau = *hs.tau;
@@ -343,15 +222,15 @@ __global__ void __launch_bounds__(256) hbm_phase_kernel(NetTables t, RunParams p
   SamplerCtx cx{rinv, p.cap, 0u};
   long long* st = reinterpret_cast<long long*>(p.stats + 5 * (int64_t)i);
   int32_t part[4] = {0, 0, 0, 0};  // Q, D, X, A per replication
-  if (phase == 0) {  // backward departures / routing / arrivals
+  if constexpr (phase == 0) {  // backward departures / routing / arrivals
     int32_t v[3] = {0, 0, 0};
     if (act) {
-      UnitOut o = backward_departures(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
+      const UnitOut o = unit_update<false>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
       v[0] = o.D; v[1] = o.X; v[2] = o.A;
       part[1] = o.D; part[2] = o.X; part[3] = o.A;
     }
     reduce_to<3>(st + 2, v, lead && su < m, 32, true);
-  } else if (phase == 1) {  // backward gather / update
+  } else if constexpr (phase == 1) {  // backward gather / update
     int32_t v[2] = {0, 0};
     if (act) {
       const int32_t nn = backward_gather(t, i, hs.N, hs.Redge, hs.ld, rloc, cx.err);
@@ -363,7 +242,7 @@ __global__ void __launch_bounds__(256) hbm_phase_kernel(NetTables t, RunParams p
   } else {  // forward level
     int32_t v[5] = {0, 0, 0, 0, 0};
     if (act) {
-      UnitOut o = forward_unit(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
+      const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
       const int32_t c = __ldg(t.servers + i);
       v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
       part[0] = o.N; part[1] = o.D; part[2] = o.X; part[3] = o.A;
@@ -435,19 +314,22 @@ int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps) {
          4 * ((int64_t)n + E) * tile_reps;
 }
 
-cudaError_t persistent_occupancy(int block, int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem);
+cudaError_t persistent_occupancy(int scheme, int block, int smem, int* blocks_per_sm) {
+  const void* fn = scheme == 0 ? (const void*)persistent_kernel<0> : (const void*)persistent_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block, int smem,
                               cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem);
+  const void* fn = p.scheme == 0 ? (const void*)persistent_kernel<0> : (const void*)persistent_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  persistent_kernel<<<grid, block, smem, s>>>(t, p);
+  if (p.scheme == 0)
+    persistent_kernel<0><<<grid, block, smem, s>>>(t, p);
+  else
+    persistent_kernel<1><<<grid, block, smem, s>>>(t, p);
   return cudaGetLastError();
 }
 
@@ -465,13 +347,13 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
   const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
   if (p.scheme == 0) {
     dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
-    hbm_phase_kernel<<<grid, block, 0, s>>>(t, p, hs, 0, 0, t.n);
-    hbm_phase_kernel<<<grid, block, 0, s>>>(t, p, hs, 1, 0, t.n);
+    hbm_phase_kernel<0><<<grid, block, 0, s>>>(t, p, hs, 0, t.n);
+    hbm_phase_kernel<1><<<grid, block, 0, s>>>(t, p, hs, 0, t.n);
   } else {
     for (int32_t j = 0; j < t.L; ++j) {
       const int32_t s0 = lvl_ptr_host[j], m = lvl_ptr_host[j + 1] - lvl_ptr_host[j];
       dim3 grid(tiles, (unsigned)((m + G - 1) / G));
-      hbm_phase_kernel<<<grid, block, 0, s>>>(t, p, hs, 2, s0, m);
+      hbm_phase_kernel<2><<<grid, block, 0, s>>>(t, p, hs, s0, m);
     }
   }
   hbm_advance_kernel<<<1, 1, 0, s>>>(hs.tau);

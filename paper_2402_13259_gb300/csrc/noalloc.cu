@@ -84,12 +84,12 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   if (K >= (1 << 24)) return noalloc_fail(EULER_ERR_TOO_LARGE, "too many steps (T/dt >= 2^24)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
 
-  // scratch layout: [err, tau] | p0[n] | lam[K][n_ex] | racc[R][4] | N[n][ld] | Redge[E][ld]
+  // scratch layout: [err, tau] | p0 constants[n] | lam[K][n_ex] | racc[R][4] | N[n][ld] | Redge[E][ld]
   const int64_t ld = (R + 3) / 4 * 4;
   const int64_t n_ex = h->n_ex > 0 ? h->n_ex : 1;
   size_t off = 256;
   const size_t off_p0 = off;
-  off = align256(off + sizeof(float) * (size_t)h->n);
+  off = align256(off + sizeof(float4) * (size_t)h->n);
   const size_t off_lam = off;
   off = align256(off + sizeof(float) * (size_t)K * (size_t)n_ex);
   const size_t off_racc = off;
@@ -113,15 +113,19 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   if (R == 0) return EULER_OK;
 
   // per-call tables, computed as euler_net_simulate computes them
-  float* d_p0 = reinterpret_cast<float*>(base + off_p0);
+  float4* d_p0 = reinterpret_cast<float4*>(base + off_p0);
   float* d_lam = reinterpret_cast<float*>(base + off_lam);
-  for (int32_t i0 = 0; i0 < h->n && e == cudaSuccess; i0 += kStage) {
-    const int32_t cnt = h->n - i0 < kStage ? h->n - i0 : kStage;
+  for (int32_t i0 = 0; i0 < h->n && e == cudaSuccess; i0 += kStage / 4) {
+    const int32_t cnt = h->n - i0 < kStage / 4 ? h->n - i0 : kStage / 4;
     for (int32_t k = 0; k < cnt; ++k) {
       const float y = (float)(h->mu[i0 + k] * dt);
-      g_stage[k] = -fm::expm1(-y);
+      const BinomConst bc = binom_const(-fm::expm1(-y));
+      g_stage[4 * k + 0] = bc.c0;
+      g_stage[4 * k + 1] = bc.q;
+      g_stage[4 * k + 2] = bc.r;
+      g_stage[4 * k + 3] = bc.lq;
     }
-    e = cudaMemcpyAsync(d_p0 + i0, g_stage, sizeof(float) * cnt, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(d_p0 + i0, g_stage, sizeof(float4) * cnt, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // staging buffer is reused
   }
   if (h->n_ex > 0) {
@@ -164,6 +168,8 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
   p.stats = stats;
   p.err = d_err;
+  p.wait_limit = (int64_t)1 << 25;
+  p.test_stall = 0;
   HbmState hs;
   hs.tau = reinterpret_cast<int32_t*>(base + 4);
   hs.racc = reinterpret_cast<int64_t*>(base + off_racc);

@@ -36,6 +36,7 @@ namespace eulernet {
 // Error bits latched in the handle's device error word.
 constexpr unsigned kErrSamplerCap = 1u;
 constexpr unsigned kErrOverflow = 2u;
+constexpr unsigned kErrStall = 4u;
 constexpr int32_t kStateLimit = 1 << 30;
 
 EN_HD float bits_f(uint32_t u) {
@@ -181,10 +182,10 @@ struct PhiloxStream {
     uint32_t k0 = key0, k1 = key1;
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-      const uint32_t lo0 = 0xD2511F53u * x0;
-      const uint32_t hi0 = __umulhi(0xD2511F53u, x0);
-      const uint32_t lo1 = 0xCD9E8D57u * x2;
-      const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2);
+      const unsigned long long m0 = (unsigned long long)0xD2511F53u * x0;  // one wide multiply
+      const unsigned long long m1 = (unsigned long long)0xCD9E8D57u * x2;
+      const uint32_t lo0 = (uint32_t)m0, hi0 = (uint32_t)(m0 >> 32);
+      const uint32_t lo1 = (uint32_t)m1, hi1 = (uint32_t)(m1 >> 32);
       const uint32_t y0 = hi1 ^ x1 ^ k0;
       const uint32_t y2 = hi0 ^ x3 ^ k1;
       x0 = y0;
@@ -212,10 +213,10 @@ struct PhiloxStream {
     return w;
   }
 
+  // (w >> 8) | 1 is the odd integer 2 (w >> 9) + 1.
   EN_D float uniform() {
     const uint32_t w = next();
-    const uint32_t odd = ((w >> 9) << 1) | 1u;
-    return (float)odd * 0x1p-24f;
+    return (float)((w >> 8) | 1u) * 0x1p-24f;
   }
 };
 
@@ -332,13 +333,45 @@ EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
   return (int32_t)floorf(lam);
 }
 
-EN_D int32_t binomial_half(int32_t n, float p, PhiloxStream& st, SamplerCtx& cx) {
+// Constants of one binomial success probability p, as the sampler uses them:
+// c0 = 0 for p <= 0 (or NaN), 2 for p >= 1, otherwise +pe or -pe where
+// pe = min(p, 1 - p) and the sign marks the symmetric case p > 1/2;
+// q = 1 - pe, r = pe / q and lq = ln(1 - pe) serve the inversion branch.
+// For a probability that is fixed per station or per edge they are computed
+// once (on the host, with these same functions); per draw otherwise.
+struct BinomConst {
+  float c0, q, r, lq;
+};
+
+EN_HD BinomConst binom_const(float p) {
+  BinomConst b;
+  if (!(p > 0.0f)) {
+    b.c0 = 0.0f;
+    b.q = b.r = b.lq = 0.0f;
+    return b;
+  }
+  if (p >= 1.0f) {
+    b.c0 = 2.0f;
+    b.q = b.r = b.lq = 0.0f;
+    return b;
+  }
+  const bool flip = p > 0.5f;
+  const float pe = flip ? 1.0f - p : p;
+  b.q = 1.0f - pe;
+  b.r = pe / b.q;
+  b.lq = fm::log1p(-pe);
+  b.c0 = flip ? -pe : pe;
+  return b;
+}
+
+// Bin(n, pe) for pe <= 1/2, q = 1 - pe: inversion for n pe < 10 (using r and
+// lq), BTRS otherwise.
+EN_D int32_t binomial_half(int32_t n, float p, float q, float r, float lq, PhiloxStream& st,
+                           SamplerCtx& cx) {
   const float nf = (float)n;
   const float np = nf * p;
-  const float q = 1.0f - p;
   if (np < 10.0f) {
-    const float r = p / q;
-    float pk = fm::exp(nf * fm::log1p(-p));
+    float pk = fm::exp(nf * lq);
     float F = pk;
     const float u = st.uniform();
     int32_t k = 0;
@@ -376,11 +409,19 @@ EN_D int32_t binomial_half(int32_t n, float p, PhiloxStream& st, SamplerCtx& cx)
   return (int32_t)floorf(np);
 }
 
+// Bin(n, p) from its constants: zero draws if n = 0 or p <= 0 (Appendix A's
+// "zero if the first argument is zero"), n if p >= 1, n - Bin(n, 1 - p) for
+// p > 1/2.
+EN_D int32_t binomial_c(int32_t n, const BinomConst& bc, PhiloxStream& st, SamplerCtx& cx) {
+  if (n <= 0 || bc.c0 == 0.0f) return 0;
+  if (bc.c0 >= 1.0f) return n;
+  const float pe = fabsf(bc.c0);
+  const int32_t k = binomial_half(n, pe, bc.q, bc.r, bc.lq, st, cx);
+  return bc.c0 < 0.0f ? n - k : k;
+}
+
 EN_D int32_t binomial(int32_t n, float p, PhiloxStream& st, SamplerCtx& cx) {
-  if (n <= 0 || !(p > 0.0f)) return 0;  // Appendix A: zero if the count is zero
-  if (p >= 1.0f) return n;
-  if (p > 0.5f) return n - binomial_half(n, 1.0f - p, st, cx);
-  return binomial_half(n, p, st, cx);
+  return binomial_c(n, binom_const(p), st, cx);
 }
 
 EN_D float std_normal(PhiloxStream& st, SamplerCtx& cx) {
@@ -427,15 +468,41 @@ EN_D float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
   return (float)k / rate;
 }
 
-// GenerateDeparture(x, m, mu, h), Lemma 1 / Algorithm 1; p0 = 1 - e^{-mu h}.
-EN_D int32_t generate_departure(int32_t x, int32_t m, float mu, float h, float p0,
-                                PhiloxStream& st, SamplerCtx& cx) {
-  if (x <= m) return binomial(x, p0, st, cx);
+// GenerateDeparture(x, m, mu, h), Lemma 1 / Algorithm 1, split at its last
+// draw: this part takes the branch (drawing T ~ Erlang(x - m, m mu) when
+// x > m) and returns the binomial that completes D = base + Bin(n, p):
+//   x <= m        : Bin(x, p0),                       p0 = 1 - e^{-mu h}
+//   x > m, T > h  : Bin(x - m - 1, h / T)
+//   x > m, T <= h : (x - m) + Bin(m, 1 - e^{-mu (h - T)})
+// Callers draw that binomial next from the same stream, so the draws are
+// exactly Algorithm 1's; lanes on either branch meet again at one binomial.
+struct BinomialArgs {
+  int32_t n;
+  BinomConst c;
+  int32_t base;
+};
+
+// p0c: the constants of p0 = 1 - e^{-mu h} of this station (fixed per call).
+EN_D BinomialArgs departure_branch(int32_t x, int32_t m, float mu, float h, const BinomConst& p0c,
+                                   PhiloxStream& st, SamplerCtx& cx) {
+  BinomialArgs b;
+  b.base = 0;
+  if (x <= m) {
+    b.n = x;
+    b.c = p0c;
+    return b;
+  }
   const float rate = (float)m * mu;
   const float T = erlang(x - m, rate, st, cx);
-  if (T > h) return binomial(x - m - 1, h / T, st, cx);
-  const float p = -fm::expm1(-(mu * (h - T)));
-  return (x - m) + binomial(m, p, st, cx);
+  if (T > h) {
+    b.n = x - m - 1;
+    b.c = binom_const(h / T);
+  } else {
+    b.n = m;
+    b.c = binom_const(-fm::expm1(-(mu * (h - T))));
+    b.base = x - m;
+  }
+  return b;
 }
 
 }  // namespace eulernet

@@ -1,0 +1,166 @@
+// unit.cuh -- one (station, replication) update of the Euler step and the
+// warp-level statistics reductions, shared by the library's kernels.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.h"
+#include "sampling.cuh"
+
+namespace eulernet {
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void latch(unsigned* err, unsigned bits) {
+  if (bits) atomicOr(err, bits);
+}
+
+__device__ __forceinline__ BinomConst as_const(float4 v) { return BinomConst{v.x, v.y, v.z, v.w}; }
+
+__device__ __forceinline__ int64_t gather_in(const NetTables& t, int32_t i, const int32_t* redge,
+                                             int64_t stride, int64_t col) {
+  int64_t s = 0;
+  const int32_t k1 = __ldg(t.in_ptr + i + 1);
+  for (int32_t k = __ldg(t.in_ptr + i); k < k1; ++k)
+    s += redge[(int64_t)__ldg(t.in_edge + k) * stride + col];
+  return s;
+}
+
+// Sum `v` over aligned segments of `w` lanes (w a power of two <= 32); the
+// segment total ends up in every lane of the segment.
+__device__ __forceinline__ unsigned seg_sum32(unsigned v, int w) {
+  if (w == 32) return __reduce_add_sync(kFull, v);
+  for (int off = w >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+__device__ __forceinline__ long long seg_sum64(long long v, int w) {
+  for (int off = w >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+// Reduce NV per-unit values over the replication segment and add them to
+// dst[0..NV) by the segment leader.  `fits` must be warp-uniform-safe: it is
+// combined with __all_sync here.  mode 0: plain add (exclusive owner), 1:
+// shared/global atomic add.
+template <int NV>
+__device__ __forceinline__ void reduce_to(long long* dst, const int32_t (&v)[NV], bool lead,
+                                          int w, bool atomic) {
+  int32_t vmax = 0;
+#pragma unroll
+  for (int s = 0; s < NV; ++s) vmax = v[s] > vmax ? v[s] : vmax;
+  const bool small = __all_sync(kFull, vmax < (1 << 27));
+  long long tot[NV];
+  if (small) {
+#pragma unroll
+    for (int s = 0; s < NV; ++s) tot[s] = (long long)seg_sum32((unsigned)v[s], w);
+  } else {
+#pragma unroll
+    for (int s = 0; s < NV; ++s) tot[s] = seg_sum64((long long)v[s], w);
+  }
+  if (lead) {
+#pragma unroll
+    for (int s = 0; s < NV; ++s) {
+      if (atomic)
+        atomicAdd(reinterpret_cast<unsigned long long*>(dst + s), (unsigned long long)tot[s]);
+      else
+        dst[s] += tot[s];
+    }
+  }
+}
+
+// ---- one unit ----------------------------------------------------------------
+
+struct UnitOut {
+  int32_t N, D, X, A;
+};
+
+// Departure then routing from input count y (Algorithm 1, then the Sec. 2.2
+// multinomial as sequential conditional binomials), all from the unit's
+// service stream.  One binomial call site serves the departure and every
+// routing edge, so lanes that took different branches of Algorithm 1 execute
+// the binomial together.
+__device__ __forceinline__ void serve_and_route(const NetTables& t, const RunParams& p, int32_t i,
+                                                uint32_t tau, uint32_t rep, int32_t y,
+                                                int32_t* redge, int64_t stride, int64_t col,
+                                                SamplerCtx& cx, int32_t& D, int32_t& X) {
+  PhiloxStream svc;
+  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
+  const BinomialArgs dep = departure_branch(y, __ldg(t.servers + i), __ldg(t.mu + i), p.h,
+                                            as_const(__ldg(p.p0 + i)), svc, cx);
+  const int32_t e0 = __ldg(t.row_ptr + i);
+  const int32_t deg = __ldg(t.row_ptr + i + 1) - e0;
+  int32_t rem = 0;
+  D = 0;
+  for (int32_t j = -1; j < deg; ++j) {
+    const int32_t nb = j < 0 ? dep.n : rem;
+    const BinomConst bc = j < 0 ? dep.c : as_const(__ldg(t.qc + e0 + j));
+    const int32_t v = binomial_c(nb, bc, svc, cx);  // Bin(0, .) draws nothing
+    if (j < 0) {
+      D = dep.base + v;
+      rem = D;
+    } else {
+      redge[(int64_t)(e0 + j) * stride + col] = v;
+      rem = rem - v;
+    }
+  }
+  X = rem;
+}
+
+// One unit of either scheme at station i.  The external-arrival draw comes
+// first: it uses its own stream, so its position does not change any draw.
+//   FULL = true  (forward, Algorithm 3): x = N_{tau-1} + A^ex + A^in, N_tau = x - D.
+//   FULL = false (backward, Algorithm 2, first phase): x = N_{tau-1};
+//                stores N_{tau-1} - D + A^ex, the gather adds A^in later.
+template <bool FULL>
+__device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunParams& p, int32_t i,
+                                               uint32_t tau, uint32_t rep, const float* lam_t,
+                                               int32_t* nstate, int32_t* redge, int64_t stride,
+                                               int64_t col, SamplerCtx& cx) {
+  UnitOut o;
+  o.A = 0;
+  const int32_t ec = __ldg(t.ex_col + i);
+  if (ec >= 0) {
+    PhiloxStream arr;
+    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
+    o.A = poisson(__ldg(lam_t + ec), arr, cx);
+  }
+  const int32_t n_prev = nstate[(int64_t)i * stride + col];
+  long long x = n_prev;
+  if (FULL) {
+    x += (long long)o.A + gather_in(t, i, redge, stride, col);
+    if (x > kStateLimit) {
+      cx.err |= kErrOverflow;
+      x = kStateLimit;
+    }
+  }
+  serve_and_route(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X);
+  if (FULL) {
+    o.N = (int32_t)x - o.D;
+    nstate[(int64_t)i * stride + col] = o.N;
+  } else {
+    long long part = (long long)n_prev - o.D + o.A;
+    if (part > 0x7fffffffLL) part = 0x7fffffffLL;
+    nstate[(int64_t)i * stride + col] = (int32_t)part;
+    o.N = 0;
+  }
+  return o;
+}
+
+// Backward second phase: N_tau = (N_{tau-1} - D + A^ex) + A^in.
+__device__ __forceinline__ int32_t backward_gather(const NetTables& t, int32_t i, int32_t* nstate,
+                                                   const int32_t* redge, int64_t stride,
+                                                   int64_t col, unsigned& err) {
+  long long nn = (long long)nstate[(int64_t)i * stride + col] + gather_in(t, i, redge, stride, col);
+  if (nn > kStateLimit) {
+    err |= kErrOverflow;
+    nn = kStateLimit;
+  }
+  nstate[(int64_t)i * stride + col] = (int32_t)nn;
+  return (int32_t)nn;
+}
+
+__device__ __forceinline__ void fill_rinv(float* rinv) {
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) rinv[k] = k ? 1.0f / (float)k : 0.0f;
+}
+
+}  // namespace eulernet

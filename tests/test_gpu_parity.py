@@ -116,9 +116,12 @@ def test_launch_shape_and_form_invariance(Bd, scheme):
     net = W.random_small_dag(rng, 24, max_deg=3, m_range=(2, 20), ext_frac=0.5, lam_scale=20.0)
     R, dt, T, seed = 200, 0.05, 2.0, 77
     ref = _gpu_stats(Bd, net, scheme, dt, T, R, seed)
-    variants = [{Bd.OPT_TILE_REPS: 1, Bd.OPT_BLOCK: 64}, {Bd.OPT_TILE_REPS: 8},
-                {Bd.OPT_TILE_REPS: 32, Bd.OPT_GRID: 1}, {Bd.OPT_TILE_REPS: 64, Bd.OPT_BLOCK: 128},
-                {Bd.OPT_FORM: 2}, {Bd.OPT_FORM: 2, Bd.OPT_GRAPH_STEPS: 7, Bd.OPT_BLOCK: 64}]
+    variants = [{Bd.OPT_FORM: 1, Bd.OPT_TILE_REPS: 1, Bd.OPT_BLOCK: 64}, {Bd.OPT_FORM: 1, Bd.OPT_TILE_REPS: 8},
+                {Bd.OPT_FORM: 1, Bd.OPT_TILE_REPS: 32, Bd.OPT_GRID: 1},
+                {Bd.OPT_FORM: 1, Bd.OPT_TILE_REPS: 64, Bd.OPT_BLOCK: 128},
+                {Bd.OPT_FORM: 2}, {Bd.OPT_FORM: 2, Bd.OPT_GRAPH_STEPS: 7, Bd.OPT_BLOCK: 64},
+                {Bd.OPT_FORM: 3, Bd.OPT_PIPE_WARPS: 1}, {Bd.OPT_FORM: 3, Bd.OPT_PIPE_WARPS: 5},
+                {Bd.OPT_FORM: 3, Bd.OPT_PIPE_WARPS: 16, Bd.OPT_GRID: 3}]
     for opt in variants:
         _assert_equal(_gpu_stats(Bd, net, scheme, dt, T, R, seed, options=opt), ref, f"options {opt}")
 
@@ -193,6 +196,28 @@ def test_sampler_cap_reports_error(Bd):
         assert ei.value.code == -5
         h.set_option(Bd.OPT_SAMPLER_CAP, -1)
         h.simulate(0, 0.01, 1.0, 64, 1)  # status was cleared; default cap works
+    finally:
+        h.close()
+
+
+def test_pipeline_wait_timeout_reports_error(Bd):
+    """A bounded inter-warp wait that runs out (the warps withhold their
+    progress on purpose) ends the kernel with EULER_ERR_STALL; the context stays usable."""
+    rng = np.random.default_rng(4)
+    net = W.random_small_dag(rng, 12, max_deg=2, m_range=(2, 9), ext_frac=0.8, lam_scale=5.0)
+    h = Bd.EulerNet(net)
+    try:
+        h.set_option(Bd.OPT_FORM, 3)
+        h.set_option(Bd.OPT_PIPE_WARPS, 4)
+        h.set_option(Bd.OPT_WAIT_LIMIT, 20000)  # roughly a few milliseconds per wait
+        h.set_option(Bd.OPT_TEST_STALL, 1)
+        with pytest.raises(Bd.EulerError) as ei:
+            h.simulate(1, 0.1, 2.0, 64, 3)
+        assert ei.value.code == -8
+        h.set_option(Bd.OPT_TEST_STALL, -1)
+        h.set_option(Bd.OPT_WAIT_LIMIT, -1)
+        ok = h.simulate(1, 0.1, 2.0, 64, 3).cpu().numpy()  # usable afterwards
+        assert ok[: 5 * 12].sum() > 0
     finally:
         h.close()
 

@@ -1,0 +1,60 @@
+"""The N>1 path on CPU: two gloo ranks each simulate their replication range
+(with the CPU oracle standing in for the device) and the combined statistics
+equal a single-process run over all replications, bit for bit."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2402_13259_gb300 import sharding
+from paper_2402_13259_gb300 import workloads as W
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, R, scaling, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import oracle as O
+        run = W.tandem3(R=R)
+        begin, count = sharding.replica_range(rank, world, R, scaling)
+        res = O.simulate(run.net, 1, run.dt, 1.5, count, run.seed, rep_begin=begin)
+        np.save(os.path.join(out_dir, f"rank{rank}.npy"), res["stats"])
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("scaling", ["strong", "weak"])
+def test_two_rank_replication_split(tmp_path, scaling):
+    world, R = 2, 37
+    port = _free_port()
+    mp.spawn(_rank_main, args=(world, port, R, scaling, str(tmp_path)), nprocs=world, join=True)
+    from oracle import oracle as O
+    run = W.tandem3(R=R)
+    ranges = [sharding.replica_range(r, world, R, scaling) for r in range(world)]
+    parts = [np.load(tmp_path / f"rank{r}.npy") for r in range(world)]
+    combined = sharding.combine_stats(parts, run.net.n, [c for _, c in ranges])
+    total = sum(c for _, c in ranges)
+    whole = O.simulate(run.net, 1, run.dt, 1.5, total, run.seed, rep_begin=0)["stats"]
+    assert np.array_equal(combined, whole)
+
+
+def test_replica_range_partition():
+    for R in (1, 7, 10000):
+        for world in (1, 2, 3, 8):
+            rs = [sharding.replica_range(r, world, R, "strong") for r in range(world)]
+            assert sum(c for _, c in rs) == R
+            assert all(rs[k][0] + rs[k][1] == rs[k + 1][0] for k in range(world - 1))
+            ws = [sharding.replica_range(r, world, R, "weak") for r in range(world)]
+            assert [b for b, _ in ws] == [r * R for r in range(world)]
