@@ -167,6 +167,64 @@ def run_reference(args):
     return 0
 
 
+def run_batch_comparison(args):
+    """512 networks of uneven size and horizon: one batched persistent launch
+    (autotuned, CUDA graph) against one euler_net_simulate launch per network,
+    same GB300, identical statistics required."""
+    import numpy as np
+    import torch
+    from paper_2402_13259_gb300 import binding as Bd
+    from paper_2402_13259_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    runs = W.batch_networks(512, T_scale=args.batch_T_scale, R_scale=args.batch_R_scale)
+    handles = [Bd.EulerNet(r.net) for r in runs]
+    spec = [(k % 2, r.dt, r.T, r.R, r.seed, 0) for k, r in enumerate(runs)]
+    units = sum(r.net.n * Bd.num_steps(r.dt, r.T) * r.R for r in runs)
+    b = Bd.Batch(handles, spec)
+    block = b.autotune()
+    stats_b = b.alloc_stats()
+    stats_s = b.alloc_stats()
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        b.run(stats_b, check=False)
+
+    def per_launch():
+        for h, sp, st in zip(handles, spec, stats_s):
+            h.simulate(sp[0], sp[1], sp[2], sp[3], sp[4], sp[5], stats=st, check=False)
+
+    times = {}
+    for name, fn in (("batched", batched), ("per_launch", per_launch)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / args.steps
+    b.status()
+    identical = all(torch.equal(x, y) for x, y in zip(stats_b, stats_s))
+    ns = sorted(r.net.n for r in runs)
+    line = {"metric": "batched vs one-network-per-launch, station-step updates/s", "impl": "ours",
+            "value": units / (times["batched"] / 1e3), "unit": UNIT,
+            "per_launch_value": units / (times["per_launch"] / 1e3),
+            "speedup": times["per_launch"] / times["batched"], "identical": identical,
+            "ms_batched": times["batched"], "ms_per_launch": times["per_launch"],
+            "steps": args.steps, "warmup": args.warmup, "block": block, "n_gpus": 1,
+            "config": {"workload": f"batch512: 512 layered DAGs, n log-uniform [5,5000] (median {ns[256]}), "
+                                   f"T ~ U[10,200] x {args.batch_T_scale}, dt in {{0.005,0.01,0.02}}, "
+                                   f"R ~ U{{100..10000}} x {args.batch_R_scale}, schemes alternate",
+                       "units_per_step": units}}
+    b.close()
+    for h in handles:
+        h.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,9 +233,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="dag100", choices=["dag100", "batch512"])
+    ap.add_argument("--batch-T-scale", type=float, default=0.1)
+    ap.add_argument("--batch-R-scale", type=float, default=0.02)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch_comparison(args)
 
     import torch
     import torch.distributed as dist

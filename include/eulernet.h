@@ -152,6 +152,50 @@ EULERNET_API int euler_net_simulate_noalloc(euler_net* net, int32_t scheme, doub
                                             int64_t replications, uint64_t seed, int64_t rep_begin,
                                             int64_t* stats, void* cuda_stream);
 
+/* ---- Batched form: many independent networks in one persistent launch ---- */
+
+/* One simulation request of a batch (see euler_net_simulate for the fields). */
+typedef struct {
+  int32_t scheme;
+  double dt, T;
+  int64_t replications;
+  uint64_t seed;
+  int64_t rep_begin;
+} euler_run;
+
+typedef struct euler_batch euler_batch; /* opaque */
+
+/* Prepare `count` runs, runs[j] on network nets[j] (host planning plus
+ * uploads of the per-run tables and the work queue; the handles must stay
+ * alive until euler_batch_destroy).  A handle may appear several times only
+ * with the same (dt, T).  Work items are (network, tile of replications),
+ * ordered by decreasing cost; per-network tile sizes fill the block.
+ * Errors: EULER_ERR_ARG, EULER_ERR_TOO_LARGE (a network whose smallest tile
+ * does not fit in shared memory), EULER_ERR_CUDA, EULER_ERR_OOM. */
+EULERNET_API int euler_batch_create(euler_batch** out, euler_net* const* nets,
+                                    const euler_run* runs, int32_t count);
+
+/* Time a few launch shapes (threads per block, shared-memory budget per CTA)
+ * on a shortened horizon and keep the fastest.  Synchronises `cuda_stream`;
+ * returns the chosen block size in *block_out (may be NULL). */
+EULERNET_API int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out);
+
+/* Run every request: stats[j] is run j's caller-owned DEVICE buffer of
+ * euler_stats_len(n_j, R_j) int64, laid out as for euler_net_simulate.  The
+ * launch (zeroing plus one persistent kernel) is captured once in a CUDA
+ * graph and replayed; a call with other stats pointers re-captures.
+ * Asynchronous on cuda_stream; device-side errors via euler_batch_status. */
+EULERNET_API int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream);
+
+/* Synchronise and return the first device-side error of any run (clears them). */
+EULERNET_API int euler_batch_status(euler_batch* b, void* cuda_stream);
+
+EULERNET_API void euler_batch_destroy(euler_batch* b);
+
+/* Convenience: create, run once, synchronise, destroy. */
+EULERNET_API int euler_net_batch_simulate(euler_net* const* nets, const euler_run* runs,
+                                          int32_t count, int64_t* const* stats, void* cuda_stream);
+
 /* Synchronise `cuda_stream`, then return and clear the latched device-side
  * status of the handle's previous calls (EULER_OK if none failed). */
 EULERNET_API int euler_net_status(euler_net* net, void* cuda_stream);

@@ -42,6 +42,11 @@ class _Arrivals(C.Structure):
                 ("table_len", C.c_int32), ("tab_dt", C.c_double)]
 
 
+class _Run(C.Structure):
+    _fields_ = [("scheme", C.c_int32), ("dt", C.c_double), ("T", C.c_double),
+                ("replications", C.c_int64), ("seed", C.c_uint64), ("rep_begin", C.c_int64)]
+
+
 _lib = None
 
 
@@ -71,6 +76,18 @@ def lib():
         L.euler_num_steps.restype = i64
         L.euler_net_simulate_noalloc.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp]
         L.euler_net_simulate_noalloc.restype = C.c_int
+        L.euler_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.POINTER(_Run), i32]
+        L.euler_batch_create.restype = C.c_int
+        L.euler_batch_autotune.argtypes = [vp, vp, C.POINTER(i32)]
+        L.euler_batch_autotune.restype = C.c_int
+        L.euler_batch_run.argtypes = [vp, C.POINTER(vp), vp]
+        L.euler_batch_run.restype = C.c_int
+        L.euler_batch_status.argtypes = [vp, vp]
+        L.euler_batch_status.restype = C.c_int
+        L.euler_batch_destroy.argtypes = [vp]
+        L.euler_batch_destroy.restype = None
+        L.euler_net_batch_simulate.argtypes = [C.POINTER(vp), C.POINTER(_Run), i32, C.POINTER(vp), vp]
+        L.euler_net_batch_simulate.restype = C.c_int
         L.euler_net_h2d_bytes.argtypes = [vp]
         L.euler_net_h2d_bytes.restype = i64
         L.euler_net_destroy.argtypes = [vp]
@@ -188,3 +205,54 @@ class EulerNet:
         _check(lib().euler_net_simulate_host(self._h, scheme, dt, T, R, seed, rep_begin, _ptr(out),
                                              C.c_void_p(_stream_ptr(stream))))
         return out
+
+
+class Batch:
+    """Many runs (network handle + run settings) in one persistent launch.
+
+    runs: sequence of (scheme, dt, T, replications, seed, rep_begin)."""
+
+    def __init__(self, nets, runs):
+        L = lib()
+        self.nets = list(nets)
+        self.runs = [tuple(r) for r in runs]
+        n = len(self.nets)
+        handles = (C.c_void_p * n)(*[h._h.value for h in self.nets])
+        rr = (_Run * n)(*[_Run(int(r[0]), float(r[1]), float(r[2]), int(r[3]), int(r[4]),
+                               int(r[5]) if len(r) > 5 else 0) for r in self.runs])
+        b = C.c_void_p()
+        _check(L.euler_batch_create(C.byref(b), handles, rr, n))
+        self._b = b
+
+    def autotune(self, stream=None) -> int:
+        blk = C.c_int32()
+        _check(lib().euler_batch_autotune(self._b, C.c_void_p(_stream_ptr(stream)), C.byref(blk)))
+        return blk.value
+
+    def alloc_stats(self):
+        import torch
+        return [torch.empty(stats_len(h.n, r[3]), dtype=torch.int64, device="cuda")
+                for h, r in zip(self.nets, self.runs)]
+
+    def run(self, stats=None, stream=None, check: bool = True):
+        if stats is None:
+            stats = self.alloc_stats()
+        ptrs = (C.c_void_p * len(stats))(*[t.data_ptr() for t in stats])
+        _check(lib().euler_batch_run(self._b, ptrs, C.c_void_p(_stream_ptr(stream))))
+        if check:
+            self.status(stream)
+        return stats
+
+    def status(self, stream=None):
+        _check(lib().euler_batch_status(self._b, C.c_void_p(_stream_ptr(stream))))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().euler_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -137,6 +137,14 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
   return EULER_OK;
 }
 
+}  // namespace
+
+int eulernet::prepare_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
+  return refresh_step_tables(h, dt, T, s);
+}
+
+namespace {
+
 struct Plan {
   int form = 1, tile_reps = 32, block = 32, grid = 1;
   int64_t smem = 0, num_tiles = 0;

@@ -1,0 +1,388 @@
+// batch.cu -- many independent networks (uneven sizes and horizons) in one
+// persistent launch fed by a work queue, planned and autotuned on the host and
+// replayed from a CUDA graph.
+//
+// Work item = (network j, tile of replications).  Network j gets a tile size
+// Rt_j (a power of two) so that its widest phase keeps the block busy
+// (forward: widest level x Rt_j ~ block; backward: all stations), reduced
+// until its tile's state fits the shared-memory budget; its per-station
+// accumulators go to a global scratch slot of the CTA when they do not fit.
+// Items are sorted by decreasing cost n_j K_j Rt_j so the last CTAs to finish
+// take the cheapest items.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "handle.h"
+#include "internal.h"
+
+using namespace eulernet;
+
+struct euler_batch {
+  int32_t count = 0;
+  std::vector<euler_net*> nets;
+  std::vector<euler_run> runs;
+  int device = 0, sm_count = 0, smem_optin = 0;
+  // current plan
+  int block = 256;
+  int64_t smem_cap = 0;  // shared-memory budget per CTA used by the plan
+  int grid = 0;
+  int smem = 0;
+  int num_items = 0;
+  int num_items_s[2] = {0, 0};  // items of each scheme: [0, n0) backward, [n0, n) forward
+  int64_t sacc_slot_len = 0;
+  std::vector<RunParams> h_runs;
+  std::vector<NetTables> h_nets;
+  std::vector<int2> h_items;
+  NetTables* d_nets = nullptr;
+  RunParams* d_runs = nullptr;
+  int2* d_items = nullptr;
+  size_t items_cap = 0;
+  int* d_counter = nullptr;
+  long long* d_sacc = nullptr;
+  size_t sacc_cap = 0;
+  // graph of the last run
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t*> graph_stats;
+  cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+int bfail(int code, const std::string& msg) {
+  set_last_error(msg.c_str());
+  return code;
+}
+
+int bcuda(cudaError_t e, const char* where) {
+  std::string m = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  set_last_error(m.c_str());
+  return e == cudaErrorMemoryAllocation ? EULER_ERR_OOM : EULER_ERR_CUDA;
+}
+
+#define BTRY(expr)                                  \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return bcuda(e_, #expr); \
+  } while (0)
+
+int64_t pow2_floor(int64_t v) {
+  int64_t p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+
+int64_t state_bytes(const euler_net* h, int64_t Rt) {
+  return 32 * Rt + 4 * ((int64_t)h->n + h->E) * Rt;
+}
+
+// Plan for a block size and a per-CTA shared-memory budget.
+int make_batch_plan(euler_batch* b, int block, int64_t cap) {
+  if (block % 32 || block < 32 || block > 512) return bfail(EULER_ERR_ARG, "batch block must be a multiple of 32 in [32, 512]");
+  cap = std::min<int64_t>(cap, b->smem_optin);
+  b->block = block;
+  b->smem_cap = cap;
+  b->h_runs.assign(b->count, RunParams{});
+  b->h_nets.assign(b->count, NetTables{});
+  b->h_items.clear();
+  int64_t smem = 256, slot = 0;
+  struct Cost { double c; int j; int64_t tile; };
+  std::vector<Cost> items;
+  for (int j = 0; j < b->count; ++j) {
+    euler_net* h = b->nets[j];
+    const euler_run& r = b->runs[j];
+    const int64_t K = euler_num_steps(r.dt, r.T);
+    const int64_t width = r.scheme == EULER_BACKWARD ? h->n : h->max_level;
+    int64_t Rt = std::max<int64_t>(32, pow2_floor(std::max<int64_t>(block / std::max<int64_t>(width, 1), 1)));
+    Rt = std::min<int64_t>(Rt, block);
+    const int64_t sacc_bytes = 48 * (int64_t)h->n;
+    // largest tile that fits: accumulators in shared memory if possible,
+    // else in the CTA's global slot
+    bool sacc_global = false, fits = false;
+    for (; Rt >= 1; Rt /= 2) {
+      if (256 + sacc_bytes + state_bytes(h, Rt) <= cap) {
+        fits = true;
+        break;
+      }
+      if (256 + state_bytes(h, Rt) <= cap) {
+        sacc_global = fits = true;
+        break;
+      }
+    }
+    if (!fits) return bfail(EULER_ERR_TOO_LARGE, "a network's smallest tile does not fit the shared-memory budget");
+    smem = std::max<int64_t>(smem, 256 + (sacc_global ? 0 : sacc_bytes) + state_bytes(h, Rt));
+    if (sacc_global) slot = std::max<int64_t>(slot, 6 * (int64_t)h->n);
+    RunParams p;
+    std::memset(&p, 0, sizeof p);
+    p.p0 = h->d_p0;
+    p.lam = h->d_lam;
+    p.h = (float)r.dt;
+    p.K = (int32_t)K;
+    p.key0 = (uint32_t)r.seed;
+    p.key1 = (uint32_t)(r.seed >> 32);
+    p.R = r.replications;
+    p.rep_begin = r.rep_begin;
+    p.scheme = r.scheme;
+    p.tile_reps = (int32_t)Rt;
+    p.num_tiles = (r.replications + Rt - 1) / Rt;
+    p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+    p.stats = nullptr;
+    p.err = h->d_err;
+    p.wait_limit = (int64_t)1 << 25;
+    p.test_stall = 0;
+    p.sacc_in_global = sacc_global ? 1 : 0;
+    b->h_runs[j] = p;
+    b->h_nets[j] = h->tables();
+    const double c = (double)h->n * (double)K * (double)Rt;
+    for (int64_t tile = 0; tile < p.num_tiles; ++tile) items.push_back({c, j, tile});
+  }
+  // backward items first, then forward; each group by decreasing cost
+  std::stable_sort(items.begin(), items.end(), [&](const Cost& a, const Cost& c) {
+    const int sa = b->runs[a.j].scheme, sc = b->runs[c.j].scheme;
+    return sa != sc ? sa < sc : a.c > c.c;
+  });
+  b->num_items_s[0] = b->num_items_s[1] = 0;
+  for (const Cost& it : items) b->num_items_s[b->runs[it.j].scheme]++;
+  if (items.size() > (size_t)INT32_MAX) return bfail(EULER_ERR_TOO_LARGE, "too many work items");
+  for (const Cost& it : items) b->h_items.push_back(make_int2(it.j, (int)it.tile));
+  b->num_items = (int)items.size();
+  b->smem = (int)smem;
+  b->sacc_slot_len = slot;
+  int per_sm = 0;
+  BTRY(batch_occupancy(block, b->smem, &per_sm));
+  if (per_sm < 1) return bfail(EULER_ERR_TOO_LARGE, "batch kernel cannot be resident");
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * b->sm_count, std::max(b->num_items, 1)));
+  // device copies
+  if (!b->d_nets) BTRY(cudaMalloc(&b->d_nets, sizeof(NetTables) * std::max(b->count, 1)));
+  if (!b->d_runs) BTRY(cudaMalloc(&b->d_runs, sizeof(RunParams) * std::max(b->count, 1)));
+  if (!b->d_counter) BTRY(cudaMalloc(&b->d_counter, 2 * sizeof(int)));
+  if ((size_t)b->num_items > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    BTRY(cudaMalloc(&b->d_items, sizeof(int2) * std::max(b->num_items, 1)));
+    b->items_cap = b->num_items;
+  }
+  const size_t sacc_need = (size_t)b->grid * (size_t)slot;
+  if (sacc_need > b->sacc_cap) {
+    cudaFree(b->d_sacc);
+    b->d_sacc = nullptr;
+    BTRY(cudaMalloc(&b->d_sacc, sizeof(long long) * sacc_need));
+    b->sacc_cap = sacc_need;
+  }
+  BTRY(cudaMemcpy(b->d_nets, b->h_nets.data(), sizeof(NetTables) * b->count, cudaMemcpyHostToDevice));
+  if (b->num_items)
+    BTRY(cudaMemcpy(b->d_items, b->h_items.data(), sizeof(int2) * b->num_items, cudaMemcpyHostToDevice));
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->graph_stats.clear();
+  return EULER_OK;
+}
+
+// Upload the run table with these stats pointers (and optionally a shortened
+// horizon for tuning).
+int upload_runs(euler_batch* b, int64_t* const* stats, int32_t k_limit) {
+  std::vector<RunParams> rp = b->h_runs;
+  for (int j = 0; j < b->count; ++j) {
+    rp[j].stats = stats[j];
+    if (k_limit > 0 && rp[j].K > k_limit) rp[j].K = k_limit;
+  }
+  BTRY(cudaMemcpy(b->d_runs, rp.data(), sizeof(RunParams) * b->count, cudaMemcpyHostToDevice));
+  return EULER_OK;
+}
+
+// Zero the queue counter and every stats buffer, then launch (capturable).
+cudaError_t enqueue(euler_batch* b, int64_t* const* stats, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), s);
+  for (int j = 0; j < b->count && e == cudaSuccess; ++j)
+    e = cudaMemsetAsync(stats[j], 0,
+                        sizeof(int64_t) * (size_t)euler_stats_len(b->nets[j]->n, b->runs[j].replications), s);
+  int off = 0;
+  for (int sc = 0; sc < 2 && e == cudaSuccess; ++sc) {
+    if (b->num_items_s[sc] > 0)
+      e = launch_batch(sc, b->d_nets, b->d_runs, b->d_items + off, b->num_items_s[sc], b->d_counter + sc,
+                       b->d_sacc, b->sacc_slot_len, b->grid, b->block, b->smem, s);
+    off += b->num_items_s[sc];
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int euler_batch_create(euler_batch** out, euler_net* const* nets, const euler_run* runs,
+                       int32_t count) {
+  if (!out) return bfail(EULER_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 0 || (count > 0 && (!nets || !runs))) return bfail(EULER_ERR_ARG, "bad batch arguments");
+  euler_batch* b = new euler_batch();
+  b->count = count;
+  b->nets.assign(nets, nets + count);
+  b->runs.assign(runs, runs + count);
+  for (int j = 0; j < count; ++j) {
+    const euler_run& r = runs[j];
+    if (!nets[j] || (r.scheme != EULER_BACKWARD && r.scheme != EULER_FORWARD) || !(r.dt > 0.0) ||
+        !(r.T > 0.0) || !std::isfinite(r.dt) || !std::isfinite(r.T) || r.replications < 0 ||
+        r.rep_begin < 0 || r.rep_begin + r.replications > ((int64_t)1 << 32) ||
+        euler_num_steps(r.dt, r.T) >= (1 << 24)) {
+      delete b;
+      return bfail(EULER_ERR_ARG, "bad run " + std::to_string(j));
+    }
+    for (int k = 0; k < j; ++k)
+      if (nets[k] == nets[j] && (runs[k].dt != r.dt || runs[k].T != r.T)) {
+        delete b;
+        return bfail(EULER_ERR_ARG, "a handle appears twice with different (dt, T)");
+      }
+  }
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+  if (e != cudaSuccess) {
+    delete b;
+    return bcuda(e, "euler_batch_create device query");
+  }
+  for (int j = 0; j < count; ++j) {
+    int rc = prepare_step_tables(nets[j], runs[j].dt, runs[j].T, nullptr);
+    if (rc) {
+      euler_batch_destroy(b);
+      return rc;
+    }
+  }
+  int rc = make_batch_plan(b, 256, 110 * 1024);
+  if (rc) {
+    euler_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return EULER_OK;
+}
+
+int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) {
+  if (!b) return bfail(EULER_ERR_ARG, "batch is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  // scratch stats buffers for the trial runs
+  std::vector<int64_t*> st(b->count, nullptr);
+  size_t total = 0;
+  for (int j = 0; j < b->count; ++j) total += (size_t)euler_stats_len(b->nets[j]->n, b->runs[j].replications);
+  int64_t* pool = nullptr;
+  BTRY(cudaMalloc(&pool, sizeof(int64_t) * std::max<size_t>(total, 1)));
+  size_t off = 0;
+  for (int j = 0; j < b->count; ++j) {
+    st[j] = pool + off;
+    off += (size_t)euler_stats_len(b->nets[j]->n, b->runs[j].replications);
+  }
+  const int blocks[3] = {128, 256, 512};
+  const int64_t caps[3] = {72 * 1024, 110 * 1024, 227 * 1024};
+  float best = -1.0f;
+  int best_block = b->block;
+  int64_t best_cap = b->smem_cap;
+  cudaEvent_t e0, e1;
+  BTRY(cudaEventCreate(&e0));
+  BTRY(cudaEventCreate(&e1));
+  int rc = EULER_OK;
+  for (int bi = 0; bi < 3 && rc == EULER_OK; ++bi)
+    for (int ci = 0; ci < 3 && rc == EULER_OK; ++ci) {
+      if (make_batch_plan(b, blocks[bi], caps[ci]) != EULER_OK) continue;
+      rc = upload_runs(b, st.data(), 48);
+      if (rc) break;
+      cudaError_t e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = enqueue(b, st.data(), s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rc = bcuda(e, "batch autotune");
+        break;
+      }
+      if (best < 0.0f || ms < best) {
+        best = ms;
+        best_block = blocks[bi];
+        best_cap = caps[ci];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(pool);
+  for (euler_net* h : b->nets) cudaMemset(h->d_err, 0, sizeof(unsigned));
+  if (rc) return rc;
+  rc = make_batch_plan(b, best_block, best_cap);
+  if (rc) return rc;
+  if (block_out) *block_out = b->block;
+  return EULER_OK;
+}
+
+int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) {
+  if (!b || (b->count > 0 && !stats)) return bfail(EULER_ERR_ARG, "bad batch run arguments");
+  for (int j = 0; j < b->count; ++j)
+    if (!stats[j]) return bfail(EULER_ERR_ARG, "a stats pointer is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const bool same = b->exec && b->graph_stats.size() == (size_t)b->count &&
+                    std::equal(b->graph_stats.begin(), b->graph_stats.end(), stats);
+  if (!same) {
+    int rc = upload_runs(b, stats, 0);
+    if (rc) return rc;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (!b->cap_stream) BTRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    BTRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue(b, stats, b->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bcuda(e != cudaSuccess ? e : e2, "batch graph capture");
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bcuda(e, "cudaGraphInstantiate");
+    b->graph_stats.assign(stats, stats + b->count);
+  }
+  BTRY(cudaGraphLaunch(b->exec, s));
+  return EULER_OK;
+}
+
+int euler_batch_status(euler_batch* b, void* cuda_stream) {
+  if (!b) return bfail(EULER_ERR_ARG, "batch is NULL");
+  int first = EULER_OK;
+  for (euler_net* h : b->nets) {
+    const int rc = euler_net_status(h, cuda_stream);
+    if (rc && !first) first = rc;
+  }
+  return first;
+}
+
+void euler_batch_destroy(euler_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  cudaFree(b->d_nets);
+  cudaFree(b->d_runs);
+  cudaFree(b->d_items);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_sacc);
+  delete b;
+}
+
+int euler_net_batch_simulate(euler_net* const* nets, const euler_run* runs, int32_t count,
+                             int64_t* const* stats, void* cuda_stream) {
+  euler_batch* b = nullptr;
+  int rc = euler_batch_create(&b, nets, runs, count);
+  if (rc) return rc;
+  rc = euler_batch_run(b, stats, cuda_stream);
+  const int st = euler_batch_status(b, cuda_stream);
+  euler_batch_destroy(b);
+  return rc ? rc : st;
+}
+
+}  // extern "C"

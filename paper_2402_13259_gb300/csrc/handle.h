@@ -69,4 +69,7 @@ namespace eulernet {
 double step_mean(const euler_net& h, int32_t i, int64_t tau, double dt);
 // Set the message euler_net_last_error() returns on this thread.
 void set_last_error(const char* msg);
+// Make the handle's per-call tables (p0 constants, Lambda) current for
+// (dt, T) on stream s; returns an EULER_* code.
+int prepare_step_tables(euler_net* h, double dt, double T, cudaStream_t s);
 }  // namespace eulernet

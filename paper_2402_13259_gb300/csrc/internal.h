@@ -42,12 +42,19 @@ struct RunParams {
   int32_t cap;        // rejection-loop cap
   int64_t wait_limit; // polls of one inter-warp wait before it gives up (pipelined form)
   int32_t test_stall; // nonzero: no warp publishes progress (tests the timeout path)
+  int32_t sacc_in_global;  // batch kernel: per-station sums in the global scratch slot
   int64_t* stats;     // output, see eulernet.h
   unsigned* err;      // latched error bits
 };
 
 // Shared-memory bytes of the persistent kernel for a tile of `tile_reps`.
 int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps);
+
+// Batched form: one persistent launch over (network, tile) work items.
+cudaError_t batch_occupancy(int block, int smem, int* blocks_per_sm);
+cudaError_t launch_batch(int scheme, const NetTables* nets, const RunParams* runs, const int2* items,
+                         int num_items, int* next_item, long long* sacc_scratch,
+                         int64_t sacc_slot_len, int grid, int block, int smem, cudaStream_t s);
 
 // Launch the persistent shared-memory kernel.
 cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block,

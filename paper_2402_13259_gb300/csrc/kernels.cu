@@ -29,21 +29,49 @@ namespace eulernet {
 
 namespace {
 
-// ---- persistent shared-memory kernel -----------------------------------------
+// Per-station sums of a CTA into the stats buffer (integer atomics, so the
+// result does not depend on the order).
+__device__ __forceinline__ void flush_station_sums(const NetTables& t, const RunParams& p,
+                                                   const long long* sacc) {
+  const int32_t n = t.n;
+  int64_t* st_nk = p.stats + 5 * (int64_t)n + 4 * p.R;
+  for (int64_t k = threadIdx.x; k < 6 * (int64_t)n; k += blockDim.x) {
+    const int64_t i = k / 6, s = k % 6;
+    const long long v = sacc[k];
+    if (v == 0) continue;
+    unsigned long long* dst =
+        reinterpret_cast<unsigned long long*>(s < 5 ? p.stats + i * 5 + s : st_nk + i);
+    atomicAdd(dst, (unsigned long long)v);
+  }
+}
 
-// Shared layout: rinv[64] f32 | sacc[n][6] i64 | racc[Rt][4] i64 | N[n][Rt] i32 | Redge[E][Rt] i32
-// SCHEME 0 = backward, 1 = forward.
+// ---- persistent shared-memory form -------------------------------------------
+
+// Pointers into a CTA's working area for one tile of `Rt` replications of one
+// network.  sacc may live in shared memory or, for networks whose per-station
+// accumulators do not fit, in a global scratch slot owned by the CTA.
+struct TileSmem {
+  float* rinv;      // [64] 1/k
+  long long* sacc;  // [n][6] per-station sums (owned by this CTA)
+  long long* racc;  // [Rt][4] per-replication sums of the tile
+  int32_t* Ns;      // [n][Rt] state
+  int32_t* Rs;      // [E][Rt] routed counts
+  int* claim;       // [2] dynamic station claims per phase parity
+};
+
+// One tile: the whole time loop for replications tile*Rt ... of network t.
+// Adds per-station sums (and N_K) into sm.sacc and writes the tile's
+// per-replication sums to p.stats.  Ends with a block barrier.
 template <int SCHEME>
-__global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p, int64_t tile,
+                                          const TileSmem& sm, SamplerCtx& cx) {
   const int32_t n = t.n;
   const int Rt = p.tile_reps;
-  float* rinv = reinterpret_cast<float*>(smem);
-  long long* sacc = reinterpret_cast<long long*>(smem + 256);
-  long long* racc = sacc + 6 * (int64_t)n;
-  int32_t* Ns = reinterpret_cast<int32_t*>(racc + 4 * (int64_t)Rt);
-  int32_t* Rs = Ns + (int64_t)n * Rt;
-
+  long long* sacc = sm.sacc;
+  long long* racc = sm.racc;
+  int32_t* Ns = sm.Ns;
+  int32_t* Rs = sm.Rs;
+  int* claim = sm.claim;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int r = tid % Rt;
   const int g0 = tid / Rt;
@@ -53,19 +81,11 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunPara
   const int gwarp = (tid & ~31) / Rt;  // group of lane 0 of this warp
   const bool lead = (lane & (w - 1)) == 0;
   const bool shared_station = Rt > 32;  // several warps per station -> atomics
-
   // With one warp per station-unit (Rt = 32) warps claim the stations of a
   // phase dynamically; claim[phase parity] counts the stations handed out.
-  __shared__ int claim[2];
   const bool dynamic = Rt == 32;
   int phase = 0;
 
-  fill_rinv(rinv);
-  for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sacc[k] = 0;
-  SamplerCtx cx{rinv, p.cap, 0u};
-  __syncthreads();
-
-  for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
     const int64_t rloc = tile * Rt + r;
     const bool rvalid = rloc < p.R;
     const uint32_t rep = (uint32_t)(p.rep_begin + rloc);
@@ -177,19 +197,90 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunPara
       if (rr < p.R) st_rep[rr * 4 + (k & 3)] = racc[k];
     }
     __syncthreads();
-  }
+}
 
-  // kernel epilogue: per-station sums
-  int64_t* st_nk = p.stats + 5 * (int64_t)n + 4 * p.R;
-  for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) {
-    const int64_t i = k / 6, s = k % 6;
-    const long long v = sacc[k];
-    if (v == 0) continue;
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(
-        s < 5 ? p.stats + i * 5 + s : st_nk + i);
-    atomicAdd(dst, (unsigned long long)v);
-  }
+// Single network: CTAs loop over the tiles.
+template <int SCHEME>
+__global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int claim[2];
+  const int32_t n = t.n;
+  const int Rt = p.tile_reps;
+  TileSmem sm;
+  sm.rinv = reinterpret_cast<float*>(smem);
+  sm.sacc = reinterpret_cast<long long*>(smem + 256);
+  sm.racc = sm.sacc + 6 * (int64_t)n;
+  sm.Ns = reinterpret_cast<int32_t*>(sm.racc + 4 * (int64_t)Rt);
+  sm.Rs = sm.Ns + (int64_t)n * Rt;
+  sm.claim = claim;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  fill_rinv(sm.rinv);
+  for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sm.sacc[k] = 0;
+  SamplerCtx cx{sm.rinv, p.cap, 0u};
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
+    tile_body<SCHEME>(t, p, tile, sm, cx);
+  flush_station_sums(t, p, sm.sacc);
   latch(p.err, cx.err);
+}
+
+// Many networks: CTAs take (network, tile) work items from a queue ordered by
+// decreasing cost.  Network j's tables are nets[j], its run runs[j] (tile
+// size, scheme, stats buffer); per-station sums go to shared memory when the
+// network's layout fits (runs[j].sacc_slot < 0) or to the CTA's slot of a
+// global scratch array otherwise.
+template <int SCHEME>
+__global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, const RunParams* runs,
+                                                       const int2* items, int num_items,
+                                                       int* next_item, long long* sacc_scratch,
+                                                       int64_t sacc_slot_len) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int claim[2];
+  __shared__ int s_item;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  float* rinv = reinterpret_cast<float*>(smem);
+  fill_rinv(rinv);
+  SamplerCtx cx{rinv, 1000, 0u};
+  unsigned err = 0;
+  unsigned* err_ptr = nullptr;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(next_item, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= num_items) break;
+    const int2 wi = items[it];
+    const NetTables t = nets[wi.x];
+    const RunParams p = runs[wi.x];
+    cx.cap = p.cap;
+    err_ptr = p.err;
+    const int32_t n = t.n;
+    const int Rt = p.tile_reps;
+    TileSmem sm;
+    sm.rinv = rinv;
+    unsigned char* base = smem + 256;
+    if (p.sacc_in_global) {
+      sm.sacc = sacc_scratch + (int64_t)blockIdx.x * sacc_slot_len;
+    } else {
+      sm.sacc = reinterpret_cast<long long*>(base);
+      base += 8 * 6 * (int64_t)n;
+    }
+    sm.racc = reinterpret_cast<long long*>(base);
+    sm.Ns = reinterpret_cast<int32_t*>(sm.racc + 4 * (int64_t)Rt);
+    sm.Rs = sm.Ns + (int64_t)n * Rt;
+    sm.claim = claim;
+    for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sm.sacc[k] = 0;
+    __syncthreads();
+    tile_body<SCHEME>(t, p, wi.y, sm, cx);
+    flush_station_sums(t, p, sm.sacc);
+    __syncthreads();
+    err |= cx.err;
+    cx.err = 0;
+    if (err && err_ptr) {
+      latch(err_ptr, err);
+      err = 0;
+    }
+  }
 }
 
 // ---- HBM-state form -------------------------------------------------------------
@@ -330,6 +421,31 @@ cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, 
     persistent_kernel<0><<<grid, block, smem, s>>>(t, p);
   else
     persistent_kernel<1><<<grid, block, smem, s>>>(t, p);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_occupancy(int block, int smem, int* blocks_per_sm) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<0>, block, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel<1>, block, smem);
+  *blocks_per_sm = a < b ? a : b;
+  return e;
+}
+
+cudaError_t launch_batch(int scheme, const NetTables* nets, const RunParams* runs, const int2* items,
+                         int num_items, int* next_item, long long* sacc_scratch,
+                         int64_t sacc_slot_len, int grid, int block, int smem, cudaStream_t s) {
+  const void* fn = scheme == 0 ? (const void*)batch_kernel<0> : (const void*)batch_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (scheme == 0)
+    batch_kernel<0><<<grid, block, smem, s>>>(nets, runs, items, num_items, next_item, sacc_scratch,
+                                              sacc_slot_len);
+  else
+    batch_kernel<1><<<grid, block, smem, s>>>(nets, runs, items, num_items, next_item, sacc_scratch,
+                                              sacc_slot_len);
   return cudaGetLastError();
 }
 

@@ -209,16 +209,20 @@ def scale_dag(s: float, L: int = 20, W: int = 100, seed: int = 2, R: int = 10000
     return Run(net, dt=1.0 / math.sqrt(s), T=T, R=R, seed=seed, name=f"scale{int(s)}")
 
 
-def batch_networks(count: int = 512, seed: int = 3, max_n: int = 5000) -> List[Run]:
+def batch_networks(count: int = 512, seed: int = 3, max_n: int = 5000, T_scale: float = 1.0,
+                   R_scale: float = 1.0) -> List[Run]:
+    """Networks of the batched workload; T_scale and R_scale shrink the
+    horizons and replication counts (at least 1 replication) while keeping
+    every network's structure."""
     rng = np.random.default_rng(seed)
     runs = []
     for j in range(count):
         n_target = int(round(math.exp(rng.uniform(math.log(5), math.log(max_n)))))
         L = max(2, int(round(math.sqrt(n_target) / 3)))
         W = max(1, int(round(n_target / L)))
-        T = float(rng.uniform(10.0, 200.0))
+        T = float(rng.uniform(10.0, 200.0)) * T_scale
         dt = float(rng.choice([0.005, 0.01, 0.02]))
-        R = int(rng.integers(100, 10001))
+        R = max(1, int(round(int(rng.integers(100, 10001)) * R_scale)))
         sub = layered_dag(L=L, W=W, seed=3 + j, R=R, T=T, dt=dt, name=f"batch{j}")
         runs.append(sub)
     return runs
