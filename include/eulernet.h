@@ -152,6 +152,32 @@ EULERNET_API int euler_net_simulate_noalloc(euler_net* net, int32_t scheme, doub
                                             int64_t replications, uint64_t seed, int64_t rep_begin,
                                             int64_t* stats, void* cuda_stream);
 
+/* ---- Likelihood-ratio (score-function) gradients ---- */
+
+/* Gradients of the two performance measures, per replication
+ *   L_1 = dt * sum_{tau, i} N_{tau,i}   (time-integrated total number in system)
+ *   L_2 = sum_{tau, i} D_{tau,i}        (total station departures)
+ * with respect to theta = (mu_1 .. mu_n, a, b, phase), the service rates and
+ * the three parameters of sinusoid arrivals (zero for table arrivals).  The
+ * paper has no gradients; the estimator is the likelihood-ratio one:
+ * grad[m][c] = mean_r L_m(r) S_r[c], S_r = sum over the replication's draws of
+ * d log p(draw)/d theta (float32 terms, float64 sums), which uses the laws of
+ * the method's own draws: Poisson arrivals (Sec. 2.1.1), the binomial and
+ * Erlang laws of GenerateDeparture (Lemma 1, Algorithm 1).
+ *   grad      DEVICE [2][n+3] double, mean of L_m S
+ *   value     DEVICE [2] double, mean of L_m
+ *   grad_var  DEVICE [2][n+3] double variance of the mean, or NULL
+ *   scores    DEVICE [R][n+3] double per-replication scores out, or NULL
+ *   stats     DEVICE stats buffer (as euler_net_simulate) out, or NULL
+ * Sums over replications run in blocks of 32 (ascending), then over blocks in
+ * ascending order, so results do not depend on the launch.  Asynchronous on
+ * cuda_stream; EULER_ERR_TOO_LARGE when a tile with its score sums does not
+ * fit in shared memory. */
+EULERNET_API int euler_net_grad(euler_net* net, int32_t scheme, double dt, double T,
+                                int64_t replications, uint64_t seed, int64_t rep_begin,
+                                double* grad, double* value, double* grad_var, double* scores,
+                                int64_t* stats, void* cuda_stream);
+
 /* ---- Batched form: many independent networks in one persistent launch ---- */
 
 /* One simulation request of a batch (see euler_net_simulate for the fields). */

@@ -455,20 +455,29 @@ static float sample_erlang(int32_t k, float rate, stream_t* st, int* err) {
  *            T <= h : (x - m) + Binomial(m, 1 - e^{-mu (h - T)})
  * p0 = 1 - e^{-mu h} is passed in (computed once per station). */
 static int32_t departure(int32_t x, int32_t m, float mu, float h, float p0, stream_t* st,
-                         int* err) {
+                         int* err, float* score_mu) {
   if (x <= m) {
     CNT(EOC_DEP_LE_M);
-    return sample_binomial(x, p0, st, err);
+    int32_t k = sample_binomial(x, p0, st, err);
+    /* d/dmu log Bin(k; x, p0(mu)), dp0/dmu = h (1 - p0):  h (k/p0 - x) */
+    if (score_mu) *score_mu = h * ((k > 0 ? (float)k / p0 : 0.0f) - (float)x);
+    return k;
   }
   float rate = (float)m * mu;
   float T = sample_erlang(x - m, rate, st, err);
+  /* d/dmu log of the Erlang(x - m, m mu) density at T:  (x - m)/mu - m T */
+  float te = (float)(x - m) / mu - (float)m * T;
   if (T > h) {
     CNT(EOC_DEP_T_GT_H);
+    if (score_mu) *score_mu = te;  /* Bin(x - m - 1, h/T) does not depend on mu */
     return sample_binomial(x - m - 1, h / T, st, err);
   }
   CNT(EOC_DEP_T_LE_H);
   float p = -eo_expm1f(-(mu * (h - T)));
-  return (x - m) + sample_binomial(m, p, st, err);
+  int32_t k2 = sample_binomial(m, p, st, err);
+  /* d/dmu log Bin(k2; m, p(mu)), dp/dmu = (h - T)(1 - p) */
+  if (score_mu) *score_mu = te + (h - T) * ((k2 > 0 ? (float)k2 / p : 0.0f) - (float)m);
+  return (x - m) + k2;
 }
 
 /* Routing (Sec. 2.2): (R_i1..R_in, R_i_exit) ~ Multinomial(D, (p_i., p_i_exit)),
@@ -548,9 +557,36 @@ static double interval_rate(const eo_net* net, int32_t i, int64_t tau, double dt
   return 0.0;
 }
 
+/* d Lambda / d (a, b, phase) for the sinusoid (zero for other kinds, and
+ * where Lambda was clamped at zero). */
+static void interval_rate_grad(const eo_net* net, int32_t i, int64_t tau, double dt, double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  if (net->arr_kind != EO_ARR_SINUSOID) return;
+  if (!(interval_rate(net, i, tau, dt) > 0.0)) return;
+  double t0 = (double)(tau - 1) * dt;
+  double t1 = (double)tau * dt;
+  double om = 6.283185307179586 / net->period;
+  double c0 = cos(om * t0 + net->phase), c1 = cos(om * t1 + net->phase);
+  double s0 = sin(om * t0 + net->phase), s1 = sin(om * t1 + net->phase);
+  g[0] = net->w[i] * ((t1 - t0) + net->b * (c0 - c1) / om);
+  g[1] = net->w[i] * net->a * ((c0 - c1) / om);
+  g[2] = net->w[i] * net->a * net->b * ((s1 - s0) / om);
+}
+
 int64_t eo_num_steps(double dt, double T) {
   double k = ceil(T / dt - 1e-9);
   return k < 1.0 ? 1 : (int64_t)k;
+}
+
+/* Per-draw score terms of one unit: the departure's mu_i term, and for an
+ * external-arrival draw (lam > 0) (A/lam - 1) dLambda/dtheta. */
+static void accumulate_scores(int32_t i, float smu, int32_t A, float lam, const float* dl,
+                              double* mu_acc, double* th_acc) {
+  mu_acc[i] += (double)smu;
+  if (lam > 0.0f) {
+    float g = (float)A / lam - 1.0f;
+    for (int k = 0; k < 3; ++k) th_acc[3 * i + k] += (double)(g * dl[k]);
+  }
 }
 
 /* Topological order by Kahn's algorithm (smallest ready index first). */
@@ -599,9 +635,14 @@ static int validate(const eo_net* net) {
   return EO_OK;
 }
 
-int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
-                int64_t rep_begin, int64_t* stats, int32_t* trace_N, int32_t* trace_D,
-                int32_t* trace_A) {
+/* The time loop of both schemes; with `scores` != NULL also the score
+ * S_r = d log p(path) / d(mu_1..mu_n, a, b, phase) of every replication
+ * ([R][n+3] doubles): float32 terms per draw, float64 sums -- mu_i terms in
+ * step order, sinusoid terms per external station in step order, then over
+ * those stations in index order. */
+static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T, int64_t R,
+                         uint64_t seed, int64_t rep_begin, int64_t* stats, int32_t* trace_N,
+                         int32_t* trace_D, int32_t* trace_A, double* scores) {
   int rc = validate(net);
   if (rc) return rc;
   if (!(dt > 0.0) || !(T > 0.0) || R < 0 || rep_begin < 0 || !stats) return EO_ERR_ARG;
@@ -647,6 +688,21 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
   for (int64_t tau = 1; tau <= K; ++tau)
     for (int32_t i = 0; i < n; ++i) lam[(tau - 1) * n + i] = (float)interval_rate(net, i, tau, dt);
 
+  float* dlam = NULL;           /* [K][n][3] */
+  double* mu_acc = NULL;        /* [n] */
+  double* th_acc = NULL;        /* [n][3] */
+  if (scores) {
+    dlam = (float*)malloc((size_t)K * (size_t)n * 3 * sizeof(float));
+    for (int64_t tau = 1; tau <= K; ++tau)
+      for (int32_t i = 0; i < n; ++i) {
+        double g[3];
+        interval_rate_grad(net, i, tau, dt, g);
+        for (int k = 0; k < 3; ++k) dlam[((tau - 1) * n + i) * 3 + k] = (float)g[k];
+      }
+    mu_acc = (double*)malloc((size_t)n * sizeof(double));
+    th_acc = (double*)malloc((size_t)n * 3 * sizeof(double));
+  }
+
   int64_t* st_station = stats;            /* [n][5] */
   int64_t* st_rep = stats + 5 * (int64_t)n; /* [R][4] */
   int64_t* st_NK = st_rep + 4 * R;        /* [n]    */
@@ -662,6 +718,11 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
   for (int64_t r = 0; r < R && !err; ++r) {
     const uint32_t rep = (uint32_t)(rep_begin + r);
     for (int32_t i = 0; i < n; ++i) N[i] = net->N0 ? net->N0[i] : 0;
+    if (scores)
+      for (int32_t i = 0; i < n; ++i) {
+        mu_acc[i] = 0.0;
+        th_acc[3 * i] = th_acc[3 * i + 1] = th_acc[3 * i + 2] = 0.0;
+      }
     for (int64_t tau = 1; tau <= K && !err; ++tau) {
       const float* lam_t = lam + (tau - 1) * n;
       if (scheme == EO_BACKWARD) {
@@ -669,10 +730,12 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
         for (int32_t i = 0; i < n; ++i) {
           stream_t svc, arr;
           stream_init(&svc, seed, 1u, (uint32_t)i, (uint32_t)tau, rep);
-          D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err);
+          float smu = 0.0f;
+          D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);
           X[i] = route(D[i], net->row_ptr[i], net->row_ptr[i + 1], qc, Redge, &svc, &err);
           stream_init(&arr, seed, 0u, (uint32_t)i, (uint32_t)tau, rep);
           A[i] = sample_poisson(lam_t[i], &arr, &err);
+          if (scores) accumulate_scores(i, smu, A[i], lam_t[i], dlam + ((tau - 1) * n + i) * 3, mu_acc, th_acc);
         }
         /* ... then task 4 once every node has routed (Algorithm 2). */
         for (int32_t i = 0; i < n; ++i) {
@@ -695,7 +758,9 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
           int64_t y = (int64_t)N[i] + A[i] + ain;
           if (y > (1 << 30)) { err = EO_ERR_OVERFLOW; y = 1 << 30; }
           stream_init(&svc, seed, 1u, (uint32_t)i, (uint32_t)tau, rep);
-          D[i] = departure((int32_t)y, net->servers[i], mu_f[i], h_f, p0[i], &svc, &err);
+          float smu = 0.0f;
+          D[i] = departure((int32_t)y, net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);
+          if (scores) accumulate_scores(i, smu, A[i], lam_t[i], dlam + ((tau - 1) * n + i) * 3, mu_acc, th_acc);
           N[i] = (int32_t)y - D[i];
           X[i] = route(D[i], net->row_ptr[i], net->row_ptr[i + 1], qc, Redge, &svc, &err);
           CNT(EOC_UNITS);
@@ -725,7 +790,15 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
       }
     }
     for (int32_t i = 0; i < n; ++i) st_NK[i] += N[i];
+    if (scores) {
+      double* sr = scores + r * (int64_t)(n + 3);
+      for (int32_t i = 0; i < n; ++i) sr[i] = mu_acc[i];
+      sr[n] = sr[n + 1] = sr[n + 2] = 0.0;
+      for (int32_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) sr[n + k] += th_acc[3 * i + k];
+    }
   }
+  free(dlam); free(mu_acc); free(th_acc);
 
   free(order); free(mu_f); free(p0); free(qc); free(in_ptr); free(in_edge); free(lam);
   free(N); free(D); free(X); free(A); free(Redge);
@@ -788,7 +861,7 @@ int eo_draw_departure(int32_t x, int32_t m, double mu, double h, uint64_t seed, 
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
     stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
-    out[j] = departure(x, m, mu_f, h_f, p0, &st, &err);
+    out[j] = departure(x, m, mu_f, h_f, p0, &st, &err, NULL);
   }
   return err;
 }
@@ -825,4 +898,63 @@ void eo_uniforms(uint64_t seed, uint32_t purpose, uint32_t station, uint32_t ste
   stream_t st;
   stream_init(&st, seed, purpose, station, step, rep);
   for (int64_t j = 0; j < count; ++j) out[j] = next_uniform(&st);
+}
+
+int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+                int64_t rep_begin, int64_t* stats, int32_t* trace_N, int32_t* trace_D,
+                int32_t* trace_A) {
+  return simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, trace_N, trace_D, trace_A,
+                       NULL);
+}
+
+/* Likelihood-ratio (score-function) gradient of the two measures
+ *   L1_r = dt * sum_{tau, i} N_{tau,i}   (time-integrated total count)
+ *   L2_r = sum_{tau, i} D_{tau,i}        (total departures)
+ * with respect to (mu_1..mu_n, a, b, phase):  grad[m][c] = mean_r L_m(r) S_r[c],
+ * value[m] = mean_r L_m(r), grad_var[m][c] = variance of that mean.  Sums over
+ * replications run in blocks of 32 consecutive replications (ascending inside
+ * a block), then over blocks in ascending order.  scores_out (may be NULL)
+ * receives S_r, [R][n+3]. */
+int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+            int64_t rep_begin, double* scores_out, double* grad, double* value, double* grad_var) {
+  if (R < 1 || !grad || !value) return EO_ERR_ARG;
+  const int32_t n = net->n;
+  const int64_t C = n + 3;
+  int64_t* stats = (int64_t*)malloc((size_t)(6 * (int64_t)n + 4 * R) * sizeof(int64_t));
+  double* sc = scores_out ? scores_out : (double*)malloc((size_t)(R * C) * sizeof(double));
+  int rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, NULL, NULL, NULL, sc);
+  if (rc == EO_OK) {
+    const int64_t* rp = stats + 5 * (int64_t)n;
+    for (int m = 0; m < 2; ++m) {
+      double vsum = 0.0;
+      for (int64_t b0 = 0; b0 < R; b0 += 32) {
+        double part = 0.0;
+        for (int64_t r = b0; r < R && r < b0 + 32; ++r)
+          part += m == 0 ? dt * (double)rp[4 * r] : (double)rp[4 * r + 1];
+        vsum += part;
+      }
+      value[m] = vsum / (double)R;
+      for (int64_t c = 0; c < C; ++c) {
+        double s = 0.0, ss = 0.0;
+        for (int64_t b0 = 0; b0 < R; b0 += 32) {
+          double part = 0.0, part2 = 0.0;
+          for (int64_t r = b0; r < R && r < b0 + 32; ++r) {
+            double L = m == 0 ? dt * (double)rp[4 * r] : (double)rp[4 * r + 1];
+            double x = L * sc[r * C + c];
+            part += x;
+            part2 += x * x;
+          }
+          s += part;
+          ss += part2;
+        }
+        double g = s / (double)R;
+        grad[m * C + c] = g;
+        if (grad_var)
+          grad_var[m * C + c] = R > 1 ? (ss - (double)R * g * g) / ((double)R * (double)(R - 1)) : 0.0;
+      }
+    }
+  }
+  if (!scores_out) free(sc);
+  free(stats);
+  return rc;
 }

@@ -73,6 +73,12 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T,
                 int64_t R, uint64_t seed, int64_t rep_begin, int64_t* stats,
                 int32_t* trace_N, int32_t* trace_D, int32_t* trace_A);
 
+/* Likelihood-ratio gradient of L1 = dt sum N and L2 = sum D with respect to
+ * (mu_1..mu_n, a, b, phase) of the sinusoid arrivals; see euler_oracle.c.
+ * grad, grad_var: [2][n+3]; value: [2]; scores_out: [R][n+3] or NULL. */
+int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+            int64_t rep_begin, double* scores_out, double* grad, double* value, double* grad_var);
+
 /* Number of Euler steps for a horizon: K = ceil(T/dt - 1e-9). */
 int64_t eo_num_steps(double dt, double T);
 

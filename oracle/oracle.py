@@ -19,7 +19,7 @@ __all__ = [
     "build_oracle", "lib", "simulate", "num_steps", "stats_split", "philox", "map_f32",
     "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
     "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
-    "BACKWARD", "FORWARD",
+    "BACKWARD", "FORWARD", "grad",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -89,6 +89,9 @@ def lib():
         L.eo_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                   C.c_int64, C.c_void_p]
         L.eo_counters_get.argtypes = [C.c_void_p]
+        L.eo_grad.restype = C.c_int
+        L.eo_grad.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
+                              C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -156,6 +159,27 @@ def simulate(net: Network, scheme: int, dt: float, T: float, R: int, seed: int,
     out = {"rc": rc, "stats": stats, "K": K}
     out.update(stats_split(stats, n, R))
     out.update(tr)
+    return out
+
+
+def grad(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, rep_begin: int = 0,
+         scores: bool = False):
+    """Likelihood-ratio gradient (see eo_grad): dict with 'grad' [2, n+3],
+    'value' [2], 'var' [2, n+3] and optionally 'scores' [R, n+3]."""
+    L = lib()
+    s, keep = _make_net(net)
+    C_ = net.n + 3
+    g = np.zeros((2, C_))
+    v = np.zeros(2)
+    var = np.zeros((2, C_))
+    sc = np.zeros((R, C_)) if scores else None
+    rc = L.eo_grad(C.byref(s), scheme, dt, T, R, seed, rep_begin, _ptr(sc), _ptr(g), _ptr(v), _ptr(var))
+    del keep
+    if rc != 0:
+        raise RuntimeError(f"oracle eo_grad failed with code {rc}")
+    out = {"grad": g, "value": v, "var": var}
+    if scores:
+        out["scores"] = sc
     return out
 
 

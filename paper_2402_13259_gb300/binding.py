@@ -88,6 +88,8 @@ def lib():
         L.euler_batch_destroy.restype = None
         L.euler_net_batch_simulate.argtypes = [C.POINTER(vp), C.POINTER(_Run), i32, C.POINTER(vp), vp]
         L.euler_net_batch_simulate.restype = C.c_int
+        L.euler_net_grad.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp, vp, vp, vp, vp]
+        L.euler_net_grad.restype = C.c_int
         L.euler_net_h2d_bytes.argtypes = [vp]
         L.euler_net_h2d_bytes.restype = i64
         L.euler_net_destroy.argtypes = [vp]
@@ -197,6 +199,28 @@ class EulerNet:
     def status(self, stream=None):
         _check(lib().euler_net_status(self._h, C.c_void_p(_stream_ptr(stream))))
 
+    def grad(self, scheme: int, dt: float, T: float, R: int, seed: int, rep_begin: int = 0,
+             scores: bool = False, stats: bool = False, stream=None, check: bool = True):
+        """Likelihood-ratio gradients (see euler_net_grad): dict of device
+        tensors 'grad' [2, n+3], 'value' [2], 'var' [2, n+3] and optionally
+        'scores' [R, n+3] and 'stats'."""
+        import torch
+        C_ = self.n + 3
+        dev = dict(dtype=torch.float64, device="cuda")
+        out = {"grad": torch.empty((2, C_), **dev), "value": torch.empty(2, **dev),
+               "var": torch.empty((2, C_), **dev)}
+        if scores:
+            out["scores"] = torch.empty((R, C_), **dev)
+        if stats:
+            out["stats"] = torch.empty(stats_len(self.n, R), dtype=torch.int64, device="cuda")
+        ptr = lambda k: C.c_void_p(out[k].data_ptr()) if k in out else None  # noqa: E731
+        _check(lib().euler_net_grad(self._h, scheme, dt, T, R, seed, rep_begin, ptr("grad"), ptr("value"),
+                                    ptr("var"), ptr("scores"), ptr("stats"),
+                                    C.c_void_p(_stream_ptr(stream))))
+        if check:
+            self.status(stream)
+        return out
+
     def simulate_host(self, scheme: int, dt: float, T: float, R: int, seed: int,
                       rep_begin: int = 0, out: Optional[np.ndarray] = None, stream=None) -> np.ndarray:
         """Run with a host-memory result buffer (the library copies it back)."""
@@ -256,3 +280,39 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _with_theta(net, theta):
+    """Copy of `net` with mu = theta[:n] and sinusoid (a, b, phase) = theta[n:]."""
+    import copy
+    th = [float(v) for v in theta]
+    net2 = copy.deepcopy(net)
+    net2.mu = np.asarray(th[: net.n], dtype=np.float64)
+    net2.arrivals.a, net2.arrivals.b, net2.arrivals.phase = th[net.n:]
+    return net2
+
+
+try:
+    import torch as _torch
+
+    class EulerMeasures(_torch.autograd.Function):
+        """(E[L_1], E[L_2]) of a network as a differentiable function of
+        theta = (mu_1..mu_n, a, b, phase); backward uses the likelihood-ratio
+        gradient computed by the forward's kernel (no stored trajectory)."""
+
+        @staticmethod
+        def forward(ctx, theta, net, scheme, dt, T, R, seed):
+            h = EulerNet(_with_theta(net, theta.detach().cpu().numpy()))
+            try:
+                out = h.grad(scheme, dt, T, R, seed)
+            finally:
+                h.close()
+            ctx.save_for_backward(out["grad"].to(theta.device, theta.dtype))
+            return out["value"].to(theta.device, theta.dtype)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (G,) = ctx.saved_tensors
+            return gout @ G, None, None, None, None, None, None
+except ImportError:  # pragma: no cover - torch is required for device memory
+    pass

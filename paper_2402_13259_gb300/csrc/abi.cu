@@ -388,6 +388,11 @@ void euler_net_destroy(euler_net* h) {
   cudaFree(h->d_Redge);
   cudaFree(h->d_racc);
   cudaFree(h->d_tau);
+  cudaFree(h->d_p0f);
+  cudaFree(h->d_dlam);
+  cudaFree(h->d_gstats);
+  cudaFree(h->d_gscores);
+  cudaFree(h->d_gpartial);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -588,6 +593,146 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
     return EULER_OK;
   }
   return run_hbm(h, t, p, pl, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+// dLambda/d(a, b, phase) of station i over step tau (sinusoid arrivals; zero
+// for a table or where Lambda is clamped at zero), in double.
+void step_mean_grad(const euler_net& h, int32_t i, int64_t tau, double dt, double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  if (h.arr_kind != EULER_ARR_SINUSOID) return;
+  if (!(step_mean(h, i, tau, dt) > 0.0)) return;
+  const double t0 = (double)(tau - 1) * dt;
+  const double t1 = (double)tau * dt;
+  const double om = 6.283185307179586 / h.period;
+  const double c0 = cos(om * t0 + h.phase), c1 = cos(om * t1 + h.phase);
+  const double s0 = sin(om * t0 + h.phase), s1 = sin(om * t1 + h.phase);
+  g[0] = h.w[i] * ((t1 - t0) + h.b * (c0 - c1) / om);
+  g[1] = h.w[i] * h.a * ((c0 - c1) / om);
+  g[2] = h.w[i] * h.a * h.b * ((s1 - s0) / om);
+}
+
+template <class T>
+int grow(T** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return EULER_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  CUDA_TRY(cudaMalloc(p, sizeof(T) * std::max<size_t>(need, 1)));
+  *cap = need;
+  return EULER_OK;
+}
+
+int refresh_grad_tables(euler_net* h, double dt, double T, cudaStream_t s) {
+  if (h->g_dt == dt && h->g_T == T) return EULER_OK;
+  const int64_t K = euler_num_steps(dt, T);
+  std::vector<float> p0f(h->n);
+  for (int32_t i = 0; i < h->n; ++i) p0f[i] = -fm::expm1(-(float)(h->mu[i] * dt));
+  std::vector<float> dl((size_t)K * std::max(h->n_ex, 1) * 3, 0.0f);
+  for (int32_t i = 0; i < h->n; ++i) {
+    const int32_t c = h->ex_col[i];
+    if (c < 0) continue;
+    for (int64_t tau = 1; tau <= K; ++tau) {
+      double g[3];
+      step_mean_grad(*h, i, tau, dt, g);
+      for (int k = 0; k < 3; ++k) dl[((size_t)(tau - 1) * h->n_ex + c) * 3 + k] = (float)g[k];
+    }
+  }
+  if (!h->d_p0f) CUDA_TRY(cudaMalloc(&h->d_p0f, sizeof(float) * (size_t)h->n));
+  int rc = grow(&h->d_dlam, &h->dlam_cap, dl.size());
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(h->d_p0f, p0f.data(), sizeof(float) * p0f.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(h->d_dlam, dl.data(), sizeof(float) * dl.size(), cudaMemcpyHostToDevice, s));
+  h->h2d_bytes += (int64_t)(sizeof(float) * (p0f.size() + dl.size()));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->g_dt = dt;
+  h->g_T = T;
+  return EULER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+                   int64_t rep_begin, double* grad, double* value, double* grad_var, double* scores,
+                   int64_t* stats, void* stream) {
+  if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
+  if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return fail(EULER_ERR_ARG, "unknown scheme");
+  if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T)) return fail(EULER_ERR_ARG, "dt and T must be finite and > 0");
+  if (R < 1 || rep_begin < 0 || !grad || !value) return fail(EULER_ERR_ARG, "bad replications, rep_begin, grad or value");
+  if (rep_begin + R > (int64_t)1 << 32) return fail(EULER_ERR_TOO_LARGE, "replication index beyond 2^32");
+  const int64_t K = euler_num_steps(dt, T);
+  if (K >= (1 << 24)) return fail(EULER_ERR_TOO_LARGE, "too many steps (T/dt >= 2^24)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = refresh_step_tables(h, dt, T, s);
+  if (rc) return rc;
+  rc = refresh_grad_tables(h, dt, T, s);
+  if (rc) return rc;
+  const int64_t C = (int64_t)h->n + 3;
+  if (!stats) {
+    rc = grow(&h->d_gstats, &h->gstats_cap, (size_t)euler_stats_len(h->n, R));
+    if (rc) return rc;
+    stats = h->d_gstats;
+  }
+  if (!scores) {
+    rc = grow(&h->d_gscores, &h->gscores_cap, (size_t)(R * C));
+    if (rc) return rc;
+    scores = h->d_gscores;
+  }
+  const int64_t nb = (R + 31) / 32;
+  rc = grow(&h->d_gpartial, &h->gpartial_cap, (size_t)(4 * nb * C + 2 * nb));
+  if (rc) return rc;
+  // tile: the largest power of two <= 32 whose state and score sums fit
+  int Rt = 32;
+  int64_t smem = 0;
+  for (; Rt >= 1; Rt /= 2) {
+    smem = persistent_smem_bytes(h->n, h->E, Rt) + grad_smem_extra(h->n, h->n_ex, Rt);
+    if (smem <= h->smem_optin) break;
+  }
+  if (Rt < 1) return fail(EULER_ERR_TOO_LARGE, "gradient tile does not fit in shared memory");
+  const int64_t m_max = scheme == EULER_BACKWARD ? h->n : h->max_level;
+  const int quantum = Rt >= 32 ? 1 : 32 / Rt;
+  const int64_t gmax = std::max<int64_t>(512 / Rt, 1);
+  const int64_t iters = (m_max + gmax - 1) / gmax;
+  int64_t G = (m_max + iters - 1) / iters;
+  G = (G + quantum - 1) / quantum * quantum;
+  if (G * Rt > 512) G = 512 / Rt;
+  const int block = (int)std::max<int64_t>(G * Rt, 32);
+  int per_sm = 0;
+  cudaError_t e = grad_occupancy(scheme, block, (int)smem, &per_sm);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient occupancy query");
+  if (per_sm < 1) return fail(EULER_ERR_TOO_LARGE, "gradient kernel cannot be resident");
+  const int64_t tiles = (R + Rt - 1) / Rt;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * h->sm_count, tiles));
+  RunParams p;
+  std::memset(&p, 0, sizeof p);
+  p.p0 = h->d_p0;
+  p.lam = h->d_lam;
+  p.h = (float)dt;
+  p.K = (int32_t)K;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.R = R;
+  p.rep_begin = rep_begin;
+  p.scheme = scheme;
+  p.tile_reps = Rt;
+  p.num_tiles = tiles;
+  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+  p.stats = stats;
+  p.err = h->d_err;
+  p.wait_limit = (int64_t)1 << 25;
+  p.p0f = h->d_p0f;
+  p.dlam = h->d_dlam;
+  p.scores = scores;
+  CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s));
+  e = launch_persistent_grad(h->tables(), p, grid, block, (int)smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
+  e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
+  return EULER_OK;
 }
 
 int euler_net_status(euler_net* h, void* stream) {

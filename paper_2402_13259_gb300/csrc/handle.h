@@ -33,6 +33,18 @@ struct euler_net {
   float* d_lam = nullptr;
   size_t lam_cap = 0;
 
+  // likelihood-ratio gradient tables of the last (dt, T) and scratch
+  double g_dt = -1.0, g_T = -1.0;
+  float* d_p0f = nullptr;
+  float* d_dlam = nullptr;
+  size_t dlam_cap = 0;
+  int64_t* d_gstats = nullptr;
+  size_t gstats_cap = 0;
+  double* d_gscores = nullptr;
+  size_t gscores_cap = 0;
+  double* d_gpartial = nullptr;
+  size_t gpartial_cap = 0;
+
   // HBM-form state
   int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr;
   int64_t* d_racc = nullptr;

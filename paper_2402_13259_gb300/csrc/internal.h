@@ -43,6 +43,10 @@ struct RunParams {
   int64_t wait_limit; // polls of one inter-warp wait before it gives up (pipelined form)
   int32_t test_stall; // nonzero: no warp publishes progress (tests the timeout path)
   int32_t sacc_in_global;  // batch kernel: per-station sums in the global scratch slot
+  // likelihood-ratio gradients (persistent form, GRAD kernels only)
+  const float* p0f;   // [n] p0 as the sampler uses it
+  const float* dlam;  // [K][n_ex][3] dLambda/d(a, b, phase)
+  double* scores;     // [R][n+3] per-replication scores out
   int64_t* stats;     // output, see eulernet.h
   unsigned* err;      // latched error bits
 };
@@ -55,6 +59,16 @@ cudaError_t batch_occupancy(int block, int smem, int* blocks_per_sm);
 cudaError_t launch_batch(int scheme, const NetTables* nets, const RunParams* runs, const int2* items,
                          int num_items, int* next_item, long long* sacc_scratch,
                          int64_t sacc_slot_len, int grid, int block, int smem, cudaStream_t s);
+
+// Gradient form of the persistent kernel (scores into p.scores) and the
+// fixed-order reduction of L_m(r) S_r over replications.
+int64_t grad_smem_extra(int32_t n, int32_t n_ex, int32_t tile_reps);
+cudaError_t grad_occupancy(int scheme, int block, int smem, int* blocks_per_sm);
+cudaError_t launch_persistent_grad(const NetTables& t, const RunParams& p, int grid, int block,
+                                   int smem, cudaStream_t s);
+cudaError_t launch_grad_reduce(int32_t n, int64_t R, double dt, const int64_t* stats,
+                               const double* scores, double* partial, double* grad, double* value,
+                               double* grad_var, cudaStream_t s);
 
 // Launch the persistent shared-memory kernel.
 cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block,

@@ -57,12 +57,28 @@ struct TileSmem {
   int32_t* Ns;      // [n][Rt] state
   int32_t* Rs;      // [E][Rt] routed counts
   int* claim;       // [2] dynamic station claims per phase parity
+  double* mu_acc;   // GRAD: [n][Rt] score sums in mu_i
+  double* th_acc;   // GRAD: [n_ex][Rt][3] score sums in (a, b, phase) per external station
 };
+
+// Score terms of one unit into the tile's accumulators (GRAD kernels).
+__device__ __forceinline__ void add_scores(const NetTables& t, const RunParams& p, const TileSmem& sm,
+                                           int32_t i, int32_t tau, int r, int Rt, const UnitOut& o) {
+  sm.mu_acc[(int64_t)i * Rt + r] += (double)o.smu;
+  if (!isnan(o.garr)) {
+    const int32_t ec = __ldg(t.ex_col + i);
+    const float* dl = p.dlam + ((int64_t)(tau - 1) * t.n_ex + ec) * 3;
+    double* th = sm.th_acc + ((int64_t)ec * Rt + r) * 3;
+    th[0] += (double)(o.garr * __ldg(dl + 0));
+    th[1] += (double)(o.garr * __ldg(dl + 1));
+    th[2] += (double)(o.garr * __ldg(dl + 2));
+  }
+}
 
 // One tile: the whole time loop for replications tile*Rt ... of network t.
 // Adds per-station sums (and N_K) into sm.sacc and writes the tile's
 // per-replication sums to p.stats.  Ends with a block barrier.
-template <int SCHEME>
+template <int SCHEME, bool GRAD = false>
 __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p, int64_t tile,
                                           const TileSmem& sm, SamplerCtx& cx) {
   const int32_t n = t.n;
@@ -92,6 +108,10 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
     for (int64_t k = tid; k < (int64_t)n * Rt; k += nthr)
       Ns[k] = t.N0 ? __ldg(t.N0 + k / Rt) : 0;
     for (int k = tid; k < 4 * Rt; k += nthr) racc[k] = 0;
+    if (GRAD) {
+      for (int64_t k = tid; k < (int64_t)n * Rt; k += nthr) sm.mu_acc[k] = 0.0;
+      for (int64_t k = tid; k < 3 * (int64_t)t.n_ex * Rt; k += nthr) sm.th_acc[k] = 0.0;
+    }
     if (tid < 2) claim[tid] = 0;
     phase = 0;
     long long q_r = 0, d_r = 0, x_r = 0, a_r = 0;
@@ -120,7 +140,8 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
           const bool act = rvalid && su < n;
           int32_t v[3] = {0, 0, 0};
           if (act) {
-            const UnitOut o = unit_update<false>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+            const UnitOut o = unit_update<false, GRAD>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+            if (GRAD) add_scores(t, p, sm, su, tau, r, Rt, o);
             v[0] = o.D;
             v[1] = o.X;
             v[2] = o.A;
@@ -158,7 +179,8 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
             const int32_t i = su < m ? __ldg(t.lvl_station + s0 + su) : 0;
             int32_t v[5] = {0, 0, 0, 0, 0};
             if (act) {
-              const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+              const UnitOut o = unit_update<true, GRAD>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+              if (GRAD) add_scores(t, p, sm, i, tau, r, Rt, o);
               const int32_t c = __ldg(t.servers + i);
               v[0] = o.N;
               v[1] = o.N < c ? o.N : c;
@@ -196,11 +218,29 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
       const int64_t rr = tile * Rt + k / 4;
       if (rr < p.R) st_rep[rr * 4 + (k & 3)] = racc[k];
     }
+    if (GRAD) {
+      // S_r: mu_i sums, then (a, b, phase) summed over external stations in order
+      const int64_t C = (int64_t)n + 3;
+      for (int64_t k = tid; k < C * Rt; k += nthr) {
+        const int rr = (int)(k % Rt);
+        const int64_t c = k / Rt;
+        const int64_t rg = tile * Rt + rr;
+        if (rg >= p.R) continue;
+        double v;
+        if (c < n) {
+          v = sm.mu_acc[c * Rt + rr];
+        } else {
+          v = 0.0;
+          for (int32_t ec = 0; ec < t.n_ex; ++ec) v += sm.th_acc[((int64_t)ec * Rt + rr) * 3 + (c - n)];
+        }
+        p.scores[rg * C + c] = v;
+      }
+    }
     __syncthreads();
 }
 
 // Single network: CTAs loop over the tiles.
-template <int SCHEME>
+template <int SCHEME, bool GRAD = false>
 __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int claim[2];
@@ -213,15 +253,82 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunPara
   sm.Ns = reinterpret_cast<int32_t*>(sm.racc + 4 * (int64_t)Rt);
   sm.Rs = sm.Ns + (int64_t)n * Rt;
   sm.claim = claim;
+  sm.mu_acc = sm.th_acc = nullptr;
+  if (GRAD) {
+    const int64_t end = (int64_t)(reinterpret_cast<unsigned char*>(sm.Rs + (int64_t)t.E * Rt) - smem);
+    sm.mu_acc = reinterpret_cast<double*>(smem + (end + 15) / 16 * 16);
+    sm.th_acc = sm.mu_acc + (int64_t)n * Rt;
+  }
   const int tid = threadIdx.x, nthr = blockDim.x;
   fill_rinv(sm.rinv);
   for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sm.sacc[k] = 0;
   SamplerCtx cx{sm.rinv, p.cap, 0u};
   __syncthreads();
   for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
-    tile_body<SCHEME>(t, p, tile, sm, cx);
+    tile_body<SCHEME, GRAD>(t, p, tile, sm, cx);
   flush_station_sums(t, p, sm.sacc);
   latch(p.err, cx.err);
+}
+
+// L_m(r) S_r[c] summed over blocks of 32 consecutive replications (ascending
+// inside a block): partial[b][m][c], partial sums of squares, and sums of L.
+// L_1(r) = dt Q_r, L_2(r) = D_r from the per-replication statistics.
+__global__ void grad_partial_kernel(int32_t n, int64_t R, double dt, const int64_t* stats,
+                                    const double* scores, double* partial) {
+  const int64_t C = (int64_t)n + 3;
+  const int64_t b = blockIdx.x;
+  const int64_t nb = gridDim.x;
+  const int64_t* rp = stats + 5 * (int64_t)n;
+  double* ps = partial + b * 2 * C;             // [nb][2][C] sums
+  double* pq = partial + nb * 2 * C + b * 2 * C;  // [nb][2][C] sums of squares
+  double* pv = partial + 4 * nb * C + b * 2;      // [nb][2] sums of L
+  for (int64_t k = threadIdx.x; k < 2 * C + 2; k += blockDim.x) {
+    if (k < 2 * C) {
+      const int m = (int)(k / C);
+      const int64_t c = k % C;
+      double s = 0.0, q = 0.0;
+      for (int64_t r = b * 32; r < R && r < b * 32 + 32; ++r) {
+        const double L = m == 0 ? dt * (double)rp[4 * r] : (double)rp[4 * r + 1];
+        const double x = L * scores[r * C + c];
+        s += x;
+        q += x * x;
+      }
+      ps[m * C + c] = s;
+      pq[m * C + c] = q;
+    } else {
+      const int m = (int)(k - 2 * C);
+      double s = 0.0;
+      for (int64_t r = b * 32; r < R && r < b * 32 + 32; ++r)
+        s += m == 0 ? dt * (double)rp[4 * r] : (double)rp[4 * r + 1];
+      pv[m] = s;
+    }
+  }
+}
+
+// Blocks summed in ascending order: grad = sum / R, value = sum L / R, and the
+// variance of the mean, (sum x^2 - R g^2) / (R (R - 1)).
+__global__ void grad_final_kernel(int32_t n, int64_t R, int64_t nb, const double* partial,
+                                  double* grad, double* value, double* grad_var) {
+  const int64_t C = (int64_t)n + 3;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 2 * C + 2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < 2 * C) {
+      double s = 0.0, q = 0.0;
+      for (int64_t b = 0; b < nb; ++b) {
+        s += partial[b * 2 * C + k];
+        q += partial[nb * 2 * C + b * 2 * C + k];
+      }
+      const double g = s / (double)R;
+      grad[k] = g;
+      if (grad_var)
+        grad_var[k] = R > 1 ? (q - (double)R * g * g) / ((double)R * (double)(R - 1)) : 0.0;
+    } else {
+      const int m = (int)(k - 2 * C);
+      double s = 0.0;
+      for (int64_t b = 0; b < nb; ++b) s += partial[4 * nb * C + b * 2 + m];
+      value[m] = s / (double)R;
+    }
+  }
 }
 
 // Many networks: CTAs take (network, tile) work items from a queue ordered by
@@ -446,6 +553,40 @@ cudaError_t launch_batch(int scheme, const NetTables* nets, const RunParams* run
   else
     batch_kernel<1><<<grid, block, smem, s>>>(nets, runs, items, num_items, next_item, sacc_scratch,
                                               sacc_slot_len);
+  return cudaGetLastError();
+}
+
+int64_t grad_smem_extra(int32_t n, int32_t n_ex, int32_t tile_reps) {
+  return 16 + 8 * ((int64_t)n + 3 * (int64_t)n_ex) * tile_reps;
+}
+
+cudaError_t grad_occupancy(int scheme, int block, int smem, int* blocks_per_sm) {
+  const void* fn = scheme == 0 ? (const void*)persistent_kernel<0, true> : (const void*)persistent_kernel<1, true>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+}
+
+cudaError_t launch_persistent_grad(const NetTables& t, const RunParams& p, int grid, int block,
+                                   int smem, cudaStream_t s) {
+  const void* fn = p.scheme == 0 ? (const void*)persistent_kernel<0, true> : (const void*)persistent_kernel<1, true>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (p.scheme == 0)
+    persistent_kernel<0, true><<<grid, block, smem, s>>>(t, p);
+  else
+    persistent_kernel<1, true><<<grid, block, smem, s>>>(t, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(int32_t n, int64_t R, double dt, const int64_t* stats,
+                               const double* scores, double* partial, double* grad, double* value,
+                               double* grad_var, cudaStream_t s) {
+  const int64_t nb = (R + 31) / 32;
+  grad_partial_kernel<<<(unsigned)nb, 128, 0, s>>>(n, R, dt, stats, scores, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  grad_final_kernel<<<8, 128, 0, s>>>(n, R, nb, partial, grad, value, grad_var);
   return cudaGetLastError();
 }
 

@@ -480,6 +480,9 @@ struct BinomialArgs {
   int32_t n;
   BinomConst c;
   int32_t base;
+  int32_t branch;  // 0: x <= m, 1: T > h, 2: T <= h
+  float T;         // the Erlang time (branches 1 and 2)
+  float p;         // the binomial's p in branch 2
 };
 
 // p0c: the constants of p0 = 1 - e^{-mu h} of this station (fixed per call).
@@ -487,6 +490,9 @@ EN_D BinomialArgs departure_branch(int32_t x, int32_t m, float mu, float h, cons
                                    PhiloxStream& st, SamplerCtx& cx) {
   BinomialArgs b;
   b.base = 0;
+  b.branch = 0;
+  b.T = 0.0f;
+  b.p = 0.0f;
   if (x <= m) {
     b.n = x;
     b.c = p0c;
@@ -494,13 +500,17 @@ EN_D BinomialArgs departure_branch(int32_t x, int32_t m, float mu, float h, cons
   }
   const float rate = (float)m * mu;
   const float T = erlang(x - m, rate, st, cx);
+  b.T = T;
   if (T > h) {
     b.n = x - m - 1;
     b.c = binom_const(h / T);
+    b.branch = 1;
   } else {
     b.n = m;
-    b.c = binom_const(-fm::expm1(-(mu * (h - T))));
+    b.p = -fm::expm1(-(mu * (h - T)));
+    b.c = binom_const(b.p);
     b.base = x - m;
+    b.branch = 2;
   }
   return b;
 }

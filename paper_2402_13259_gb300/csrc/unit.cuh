@@ -72,6 +72,8 @@ __device__ __forceinline__ void reduce_to(long long* dst, const int32_t (&v)[NV]
 
 struct UnitOut {
   int32_t N, D, X, A;
+  float smu;   // score term of the departure in mu_i (GRAD only)
+  float garr;  // A/Lambda - 1 of an external-arrival draw, NaN if none (GRAD only)
 };
 
 // Departure then routing from input count y (Algorithm 1, then the Sec. 2.2
@@ -79,10 +81,11 @@ struct UnitOut {
 // service stream.  One binomial call site serves the departure and every
 // routing edge, so lanes that took different branches of Algorithm 1 execute
 // the binomial together.
+template <bool GRAD>
 __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunParams& p, int32_t i,
                                                 uint32_t tau, uint32_t rep, int32_t y,
                                                 int32_t* redge, int64_t stride, int64_t col,
-                                                SamplerCtx& cx, int32_t& D, int32_t& X) {
+                                                SamplerCtx& cx, int32_t& D, int32_t& X, float& smu) {
   PhiloxStream svc;
   svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
   const BinomialArgs dep = departure_branch(y, __ldg(t.servers + i), __ldg(t.mu + i), p.h,
@@ -98,6 +101,20 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
     if (j < 0) {
       D = dep.base + v;
       rem = D;
+      if (GRAD) {
+        // d/dmu_i of the log-probability of this departure (float32):
+        //   x <= m : Bin(x, p0(mu)), dp0/dmu = h(1 - p0)        -> h (k/p0 - x)
+        //   x >  m : Erlang(x - m, m mu) density at T            -> (x - m)/mu - m T
+        //            plus, if T <= h, Bin(m, p(mu)), dp/dmu = (h - T)(1 - p) -> (h - T)(k/p - m)
+        const int32_t m = __ldg(t.servers + i);
+        if (dep.branch == 0) {
+          smu = p.h * ((v > 0 ? (float)v / __ldg(p.p0f + i) : 0.0f) - (float)y);
+        } else {
+          const float mu = __ldg(t.mu + i);
+          const float te = (float)(y - m) / mu - (float)m * dep.T;
+          smu = dep.branch == 1 ? te : te + (p.h - dep.T) * ((v > 0 ? (float)v / dep.p : 0.0f) - (float)m);
+        }
+      }
     } else {
       redge[(int64_t)(e0 + j) * stride + col] = v;
       rem = rem - v;
@@ -111,18 +128,22 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
 //   FULL = true  (forward, Algorithm 3): x = N_{tau-1} + A^ex + A^in, N_tau = x - D.
 //   FULL = false (backward, Algorithm 2, first phase): x = N_{tau-1};
 //                stores N_{tau-1} - D + A^ex, the gather adds A^in later.
-template <bool FULL>
+template <bool FULL, bool GRAD = false>
 __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunParams& p, int32_t i,
                                                uint32_t tau, uint32_t rep, const float* lam_t,
                                                int32_t* nstate, int32_t* redge, int64_t stride,
                                                int64_t col, SamplerCtx& cx) {
   UnitOut o;
   o.A = 0;
+  o.smu = 0.0f;
+  o.garr = __int_as_float(0x7fc00000);
   const int32_t ec = __ldg(t.ex_col + i);
   if (ec >= 0) {
     PhiloxStream arr;
     arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
-    o.A = poisson(__ldg(lam_t + ec), arr, cx);
+    const float lam = __ldg(lam_t + ec);
+    o.A = poisson(lam, arr, cx);
+    if (GRAD && lam > 0.0f) o.garr = (float)o.A / lam - 1.0f;  // d log Poisson / d Lambda * Lambda / Lambda
   }
   const int32_t n_prev = nstate[(int64_t)i * stride + col];
   long long x = n_prev;
@@ -133,7 +154,7 @@ __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunPara
       x = kStateLimit;
     }
   }
-  serve_and_route(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X);
+  serve_and_route<GRAD>(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X, o.smu);
   if (FULL) {
     o.N = (int32_t)x - o.D;
     nstate[(int64_t)i * stride + col] = o.N;

@@ -20,8 +20,7 @@ MUTANTS = [
     ("alg1_tail_count", "return sample_binomial(x - m - 1, h / T, st, err);",
      "return sample_binomial(x - m, h / T, st, err);"),
     # Algorithm 1, T <= h branch: the x - m already served are dropped
-    ("alg1_served_dropped", "return (x - m) + sample_binomial(m, p, st, err);",
-     "return sample_binomial(m, p, st, err);"),
+    ("alg1_served_dropped", "return (x - m) + k2;", "return k2;"),
     # Lemma 1: Erlang rate m*mu written as mu
     ("erlang_rate", "float rate = (float)m * mu;", "float rate = mu;"),
     # Lemma 1(1): the x <= m test off by one.  (x < m would be no mistake: at
@@ -31,8 +30,15 @@ MUTANTS = [
     ("route_unconditional", "double q = suffix > 0.0 ? net->prob[e] / suffix : 0.0;",
      "double q = net->prob[e];"),
     # backward scheme: departures drawn after adding the step's arrivals
-    ("backward_order", "D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err);",
-     "D[i] = departure(N[i] + (int32_t)(lam_t[i] > 0.0f ? 1 : 0), net->servers[i], mu_f[i], h_f, p0[i], &svc, &err);"),
+    ("backward_order", "D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);",
+     "D[i] = departure(N[i] + (int32_t)(lam_t[i] > 0.0f ? 1 : 0), net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);"),
+    # likelihood-ratio score of the x <= m binomial: dp0/dmu factor dropped
+    ("score_binomial", "if (score_mu) *score_mu = h * ((k > 0 ? (float)k / p0 : 0.0f) - (float)x);",
+     "if (score_mu) *score_mu = ((k > 0 ? (float)k / p0 : 0.0f) - (float)x);"),
+    # likelihood-ratio score of the Erlang density: sign slip
+    ("score_erlang", "float te = (float)(x - m) / mu - (float)m * T;", "float te = (float)(x - m) / mu + (float)m * T;"),
+    # likelihood-ratio score of the Poisson arrivals: the -1 dropped
+    ("score_poisson", "float g = (float)A / lam - 1.0f;", "float g = (float)A / lam;"),
     # forward scheme: internal arrivals left out of the departure input
     ("forward_missing_ain", "int64_t y = (int64_t)N[i] + A[i] + ain;", "int64_t y = (int64_t)N[i] + A[i];"),
     # arrival integral: sign of the sinusoid term flipped

@@ -471,3 +471,100 @@ def test_validation_errors(orc):
     row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, 1.5)])
     bad = W.Network(2, row_ptr, col, prob, np.array([1, 1]), np.array([1.0, 1.0]), arr)
     assert orc.simulate(bad, 0, 0.1, 1.0, 2, 1, expect_ok=False)["rc"] == -1
+
+
+# ---------------------------------------------------------------------------
+# Likelihood-ratio gradients (outside the paper: the paper never
+# differentiates; the score terms follow from the laws the method samples)
+# ---------------------------------------------------------------------------
+def _queueing_net():
+    """Two-station tandem with few servers and fast service, so that every
+    branch of Algorithm 1 (x <= m, T > h, T <= h) occurs often."""
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, 0.7)])
+    arr = W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([6.0, 0.0]), a=1.2, b=0.4, period=3.0, phase=0.5)
+    return W.Network(2, row_ptr, col, prob, np.array([2, 3]), np.array([2.5, 1.7]), arr)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_score_has_mean_zero(orc, scheme):
+    """E[d log p(path)/d theta] = 0 for every parameter: each per-draw score
+    term (binomial in p0(mu), Erlang density, binomial in p(mu, T), Poisson
+    in Lambda(a, b, phase)) must be the derivative of its own log-law."""
+    net = _queueing_net()
+    R = 40000
+    orc.counters_reset()
+    g = orc.grad(net, scheme, 0.3, 3.0, R, 17, scores=True)
+    c = orc.counters()
+    assert c["dep_le_m"] > 0 and c["dep_t_gt_h"] > 0 and c["dep_t_le_h"] > 0
+    sc = g["scores"]
+    z = sc.mean(axis=0) / (sc.std(axis=0) / math.sqrt(R))
+    assert np.abs(z).max() < 4.5, z
+
+
+def _inf_server_measures(net, scheme, dt, K, theta=None, mu=None):
+    """Exact E[L1] = dt sum E[N] and E[L2] = sum E[D] when no station queues."""
+    import copy
+    net2 = copy.deepcopy(net)
+    if mu is not None:
+        net2.mu = np.asarray(mu, dtype=float)
+    if theta is not None:
+        net2.arrivals.a, net2.arrivals.b, net2.arrivals.phase = theta
+    a = net2.arrivals
+    om = 2 * math.pi / a.period
+    stay = np.exp(-net2.mu * dt)
+    m = np.zeros(net2.n)
+    L1 = L2 = 0.0
+    for tau in range(1, K + 1):
+        t0, t1 = (tau - 1) * dt, tau * dt
+        lam = a.w * a.a * ((t1 - t0) + a.b * (math.cos(om * t0 + a.phase) - math.cos(om * t1 + a.phase)) / om)
+        if scheme == 0:
+            d = (1 - stay) * m
+            new = m - d + lam
+            for k in range(net2.n):
+                for e in range(net2.row_ptr[k], net2.row_ptr[k + 1]):
+                    new[net2.col[e]] += net2.prob[e] * d[k]
+            m = new
+        else:
+            y = m + lam
+            d = np.zeros(net2.n)
+            for k in range(net2.n):
+                d[k] = (1 - stay[k]) * y[k]
+                for e in range(net2.row_ptr[k], net2.row_ptr[k + 1]):
+                    y[net2.col[e]] += net2.prob[e] * d[k]
+            m = y - d
+        L1 += dt * m.sum()
+        L2 += d.sum()
+    return np.array([L1, L2])
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_gradient_matches_infinite_server_closed_form(orc, scheme):
+    """With no queueing the means are exact linear recursions; their
+    derivatives (central differences of the deterministic recursion) must lie
+    inside the LR estimate's confidence interval, for every mu_i and theta."""
+    rng = np.random.default_rng(8)
+    net = W.random_small_dag(rng, 4, max_deg=2, ext_frac=1.0, lam_scale=8.0)
+    net.servers[:] = 1_000_000
+    net.arrivals.a, net.arrivals.b, net.arrivals.phase = 1.0, 0.5, 0.3
+    dt, K, R = 0.1, 30, 60000
+    g = orc.grad(net, scheme, dt, K * dt, R, 23)
+    base = _inf_server_measures(net, scheme, dt, K)
+    assert np.all(np.abs(g["value"] - base) < 0.02 * base)
+    want = np.zeros((2, net.n + 3))
+    eps = 1e-5
+    for i in range(net.n):
+        up, dn = net.mu.copy(), net.mu.copy()
+        up[i] += eps
+        dn[i] -= eps
+        want[:, i] = (_inf_server_measures(net, scheme, dt, K, mu=up) -
+                      _inf_server_measures(net, scheme, dt, K, mu=dn)) / (2 * eps)
+    th = np.array([net.arrivals.a, net.arrivals.b, net.arrivals.phase])
+    for k in range(3):
+        up, dn = th.copy(), th.copy()
+        up[k] += eps
+        dn[k] -= eps
+        want[:, net.n + k] = (_inf_server_measures(net, scheme, dt, K, theta=up) -
+                              _inf_server_measures(net, scheme, dt, K, theta=dn)) / (2 * eps)
+    se = np.sqrt(g["var"])
+    z = (g["grad"] - want) / np.maximum(se, 1e-12)
+    assert np.abs(z).max() < 5.0, z
