@@ -34,7 +34,9 @@ SMS = 152
 LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
 # DRAM bytes per launch of the persistent kernel from ncu (profiles/), valid for
 # the kernel sources with this hash; None when the sources changed since.
-TRAFFIC = {"hash": None, "bytes_per_launch": None}
+# profiles/persistent_kernel_dag100.md: 372 KB and 220 KB per launch of 2.05e8
+# units (backward, forward), scaled to 1e10 units by the unit count.
+TRAFFIC = {"hash": "04c15bc95ae45b57", "bytes_per_launch": 0.5 * (372e3 + 220e3) * 1e10 / 2.048e8}
 
 
 def kernel_hash() -> str:
@@ -45,15 +47,20 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def workload():
+def workload(args=None):
     from paper_2402_13259_gb300 import workloads as W
-    return W.layered_dag()
+    run = W.layered_dag()
+    if args is not None and args.replications:
+        run.R = args.replications
+    if args is not None and args.horizon:
+        run.T = args.horizon
+    return run
 
 
 def config_dict(run, K, world):
     return {
-        "workload": "dag100: 100-station layered random DAG (10x10), R=10000 replications, "
-                    "T=100, dt=0.01 (K=10000 steps), backward + forward scheme per step",
+        "workload": f"dag100: 100-station layered random DAG (10x10), R={run.R} replications, "
+                    f"T={run.T:g}, dt={run.dt:g} (K={K} steps), backward + forward scheme per step",
         "stations": run.net.n, "edges": run.net.nnz, "replications_per_gpu": run.R,
         "steps_K": K, "schemes": ["backward", "forward"],
         "state": "int32 station counts, int64 statistics, float32 samplers",
@@ -140,7 +147,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import oracle as O
-    run = workload()
+    run = workload(args)
     K = O.num_steps(run.dt, run.T)
     reps = 2
     units_per_step = 2 * run.net.n * K * reps
@@ -236,6 +243,9 @@ def main():
     ap.add_argument("--workload", default="dag100", choices=["dag100", "batch512"])
     ap.add_argument("--batch-T-scale", type=float, default=0.1)
     ap.add_argument("--batch-R-scale", type=float, default=0.02)
+    ap.add_argument("--replications", type=int, default=0,
+                    help="replications of the 100-station workload (default 10000)")
+    ap.add_argument("--horizon", type=float, default=0.0, help="horizon T (default 100)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -253,7 +263,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2402_13259_gb300 import binding as Bd
-    run = workload()
+    run = workload(args)
     K = Bd.num_steps(run.dt, run.T)
     n, R = run.net.n, run.R
     from paper_2402_13259_gb300 import sharding
