@@ -152,6 +152,24 @@ EULERNET_API int euler_net_simulate_noalloc(euler_net* net, int32_t scheme, doub
                                             int64_t replications, uint64_t seed, int64_t rep_begin,
                                             int64_t* stats, void* cuda_stream);
 
+/* ---- Average scheme and step-size rule ---- */
+
+/* The average scheme (Sec. 7.1: backward and forward run side by side and
+ * their customer counts averaged): runs both schemes on the same random
+ * streams (common random numbers) into the caller's DEVICE buffers stats_b and
+ * stats_f (int64, layout of euler_net_simulate, either may be NULL to use
+ * internal scratch) and writes stats_avg (DEVICE double, same layout) =
+ * (stats_b + stats_f) / 2.  Asynchronous on cuda_stream. */
+EULERNET_API int euler_net_simulate_average(euler_net* net, double dt, double T,
+                                            int64_t replications, uint64_t seed,
+                                            int64_t rep_begin, double* stats_avg,
+                                            int64_t* stats_b, int64_t* stats_f, void* cuda_stream);
+
+/* Step-size selection rule (Sec. 5.4): h = alpha / max_i mu_i.  alpha <= 0
+ * takes the experiments' alpha = 0.4 / sqrt(max_i m_i) (Sec. 7.4).  Returns
+ * the step, or a negative value for a NULL handle. */
+EULERNET_API double euler_net_select_dt(const euler_net* net, double alpha);
+
 /* ---- Likelihood-ratio (score-function) gradients ---- */
 
 /* Gradients of the two performance measures, per replication
@@ -242,11 +260,29 @@ enum {
   EULER_OPT_WAIT_LIMIT = 7,  /* polls before an inter-warp wait of the
                                 pipelined form gives up (default 2^25, about
                                 2-4 s); then EULER_ERR_STALL                   */
-  EULER_OPT_TEST_STALL = 8   /* testing only: nonzero makes every warp of the
+  EULER_OPT_TEST_STALL = 8,  /* testing only: nonzero makes every warp of the
                                 pipelined form withhold its progress, so the
                                 warps' bounded waits run out                  */
+  EULER_OPT_WAIT_SLEEP = 9,  /* nanoseconds between polls of an inter-warp
+                                wait of the pipelined form (default 64)       */
+  EULER_OPT_DEPARTURE = 10   /* departure sampler: 0 = exact (Lemma 1,
+                                Algorithm 1), 1 = Eq. (1) D = min(x,
+                                Poisson(min(x, m) mu h)), 2 = Eq. (2)
+                                (binomial for x <= m, Eq. (1) otherwise); the
+                                biased modes are for speed/bias studies and
+                                are not available to euler_net_grad           */
 };
 EULERNET_API int euler_net_set_option(euler_net* net, int32_t option, int64_t value);
+
+/* Time-varying staffing (Sec. 2.1.2): m_i(t) = table[j*n + i] for
+ * j = min(floor(t / tab_dt), len - 1), all entries >= 1.  A step uses the
+ * servers at its start time, so staffing changes should fall on step
+ * boundaries (the paper places a boundary at each change); customers whose
+ * server is withdrawn simply wait again (the state is a count).  NULL or
+ * len = 0 returns to the constant servers of euler_net_create.  Host copy;
+ * applies to later calls. */
+EULERNET_API int euler_net_set_servers_schedule(euler_net* net, const int32_t* table, int32_t len,
+                                                double tab_dt);
 
 /* Describe the launch the next euler_net_simulate would make for these
  * sizes: form (1, 2 or 3), tile replications, block, grid, shared bytes.

@@ -28,6 +28,13 @@ void eo_counters_get(int64_t out[EOC_COUNT]) { memcpy(out, g_cnt, sizeof g_cnt);
 static int32_t g_cap = 1000;  /* rejection-loop iteration cap */
 int32_t eo_set_cap(int32_t cap) { int32_t o = g_cap; g_cap = cap > 0 ? cap : 1; return o; }
 
+static int32_t g_dep_mode = 0;  /* 0 exact, 1 Eq. (1), 2 Eq. (2) */
+int32_t eo_set_departure_mode(int32_t mode) {
+  int32_t o = g_dep_mode;
+  g_dep_mode = (mode >= 0 && mode <= 2) ? mode : 0;
+  return o;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11, "Parallel random      */
 /* numbers: as easy as 1, 2, 3").  Ten rounds; the key is bumped by the     */
@@ -454,8 +461,16 @@ static float sample_erlang(int32_t k, float rate, stream_t* st, int* err) {
  *            T >  h : Binomial(x - m - 1, h / T)
  *            T <= h : (x - m) + Binomial(m, 1 - e^{-mu (h - T)})
  * p0 = 1 - e^{-mu h} is passed in (computed once per station). */
-static int32_t departure(int32_t x, int32_t m, float mu, float h, float p0, stream_t* st,
-                         int* err, float* score_mu) {
+static int32_t departure(int32_t x, int32_t m, float mu, float h, float p0, float muh,
+                         stream_t* st, int* err, float* score_mu) {
+  if (g_dep_mode == 1 || (g_dep_mode == 2 && x > m)) {
+    /* Eq. (1): the busy count frozen at b = min(x, m) over the step,
+       D = min(x, S) with S ~ Poisson(b mu h) (Eq. (2) keeps this for x > m) */
+    int32_t b = x < m ? x : m;
+    int32_t S = sample_poisson((float)b * muh, st, err);
+    if (score_mu) *score_mu = 0.0f;
+    return S < x ? S : x;
+  }
   if (x <= m) {
     CNT(EOC_DEP_LE_M);
     int32_t k = sample_binomial(x, p0, st, err);
@@ -630,6 +645,11 @@ static int validate(const eo_net* net) {
     if (s > 1.0 + 1e-12) return EO_ERR_ARG;
   }
   if (net->arr_kind == EO_ARR_SINUSOID && (!net->w || !(net->period > 0.0))) return EO_ERR_ARG;
+  if (net->sv_table) {
+    if (net->sv_len < 1 || !(net->sv_dt > 0.0)) return EO_ERR_ARG;
+    for (int64_t k = 0; k < (int64_t)net->sv_len * net->n; ++k)
+      if (net->sv_table[k] < 1) return EO_ERR_ARG;
+  }
   if (net->arr_kind == EO_ARR_TABLE && (!net->table || net->table_len < 1 || !(net->tab_dt > 0.0)))
     return EO_ERR_ARG;
   return EO_OK;
@@ -659,10 +679,12 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
   /* per-station float parameters */
   float* mu_f = (float*)malloc((size_t)n * sizeof(float));
   float* p0 = (float*)malloc((size_t)n * sizeof(float));
+  float* muh = (float*)malloc((size_t)n * sizeof(float));
   const float h_f = (float)dt;
   for (int32_t i = 0; i < n; ++i) {
     mu_f[i] = (float)net->mu[i];
     float y = (float)(net->mu[i] * dt);
+    muh[i] = y;
     p0[i] = -eo_expm1f(-y);
   }
   float* qc = (float*)malloc((size_t)(E > 0 ? E : 1) * sizeof(float));
@@ -725,13 +747,20 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
       }
     for (int64_t tau = 1; tau <= K && !err; ++tau) {
       const float* lam_t = lam + (tau - 1) * n;
+      /* servers of this step: the schedule at the step's start time */
+      const int32_t* m_t = net->servers;
+      if (net->sv_table) {
+        int64_t j = (int64_t)floor((double)(tau - 1) * dt / net->sv_dt);
+        if (j > net->sv_len - 1) j = net->sv_len - 1;
+        m_t = net->sv_table + j * n;
+      }
       if (scheme == EO_BACKWARD) {
         /* Sec. 2.2 backward tasks 1-3 for every node from N_{tau-1} ... */
         for (int32_t i = 0; i < n; ++i) {
           stream_t svc, arr;
           stream_init(&svc, seed, 1u, (uint32_t)i, (uint32_t)tau, rep);
           float smu = 0.0f;
-          D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);
+          D[i] = departure(N[i], m_t[i], mu_f[i], h_f, p0[i], muh[i], &svc, &err, &smu);
           X[i] = route(D[i], net->row_ptr[i], net->row_ptr[i + 1], qc, Redge, &svc, &err);
           stream_init(&arr, seed, 0u, (uint32_t)i, (uint32_t)tau, rep);
           A[i] = sample_poisson(lam_t[i], &arr, &err);
@@ -759,7 +788,7 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
           if (y > (1 << 30)) { err = EO_ERR_OVERFLOW; y = 1 << 30; }
           stream_init(&svc, seed, 1u, (uint32_t)i, (uint32_t)tau, rep);
           float smu = 0.0f;
-          D[i] = departure((int32_t)y, net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);
+          D[i] = departure((int32_t)y, m_t[i], mu_f[i], h_f, p0[i], muh[i], &svc, &err, &smu);
           if (scores) accumulate_scores(i, smu, A[i], lam_t[i], dlam + ((tau - 1) * n + i) * 3, mu_acc, th_acc);
           N[i] = (int32_t)y - D[i];
           X[i] = route(D[i], net->row_ptr[i], net->row_ptr[i + 1], qc, Redge, &svc, &err);
@@ -771,7 +800,7 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
       for (int32_t i = 0; i < n; ++i) {
         int64_t* ss = st_station + 5 * (int64_t)i;
         ss[0] += N[i];
-        ss[1] += N[i] < net->servers[i] ? N[i] : net->servers[i];
+        ss[1] += N[i] < m_t[i] ? N[i] : m_t[i];
         ss[2] += D[i];
         ss[3] += X[i];
         ss[4] += A[i];
@@ -800,7 +829,7 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
   }
   free(dlam); free(mu_acc); free(th_acc);
 
-  free(order); free(mu_f); free(p0); free(qc); free(in_ptr); free(in_edge); free(lam);
+  free(order); free(mu_f); free(p0); free(muh); free(qc); free(in_ptr); free(in_edge); free(lam);
   free(N); free(D); free(X); free(A); free(Redge);
   return err;
 }
@@ -861,7 +890,7 @@ int eo_draw_departure(int32_t x, int32_t m, double mu, double h, uint64_t seed, 
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
     stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
-    out[j] = departure(x, m, mu_f, h_f, p0, &st, &err, NULL);
+    out[j] = departure(x, m, mu_f, h_f, p0, (float)(mu * h), &st, &err, NULL);
   }
   return err;
 }
@@ -917,7 +946,7 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
  * receives S_r, [R][n+3]. */
 int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
             int64_t rep_begin, double* scores_out, double* grad, double* value, double* grad_var) {
-  if (R < 1 || !grad || !value) return EO_ERR_ARG;
+  if (R < 1 || !grad || !value || g_dep_mode != 0) return EO_ERR_ARG;
   const int32_t n = net->n;
   const int64_t C = n + 3;
   int64_t* stats = (int64_t*)malloc((size_t)(6 * (int64_t)n + 4 * R) * sizeof(int64_t));

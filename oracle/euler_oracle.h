@@ -60,7 +60,17 @@ typedef struct {
   int32_t table_len;
   double tab_dt;
   const int32_t* N0;       /* [n] initial state, or NULL for an empty net  */
+  /* optional staffing schedule (Sec. 2.1.2): m_i(t) = sv_table[j*n + i] for
+     j = min(floor(t / sv_dt), sv_len - 1); a step uses m at its start time */
+  const int32_t* sv_table;
+  int32_t sv_len;
+  double sv_dt;
 } eo_net;
+
+/* Departure sampler: 0 = exact (Lemma 1, Algorithm 1), 1 = Eq. (1)
+ * D = min(x, Poisson(min(x, m) mu h)), 2 = Eq. (2) (binomial for x <= m,
+ * Eq. (1) otherwise).  Returns the previous mode. */
+int32_t eo_set_departure_mode(int32_t mode);
 
 /* Stats layout (int64), all sums over steps tau = 1..K of post-update values:
  *   [n][5]  per station  {Q_i = sum N, B_i = sum min(N, m_i), D_i = sum D,

@@ -19,7 +19,7 @@ __all__ = [
     "build_oracle", "lib", "simulate", "num_steps", "stats_split", "philox", "map_f32",
     "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
     "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
-    "BACKWARD", "FORWARD", "grad",
+    "BACKWARD", "FORWARD", "grad", "set_departure_mode",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,6 +57,7 @@ class _Net(C.Structure):
         ("w", C.c_void_p), ("a", C.c_double), ("b", C.c_double), ("period", C.c_double),
         ("phase", C.c_double), ("table", C.c_void_p), ("table_len", C.c_int32),
         ("tab_dt", C.c_double), ("N0", C.c_void_p),
+        ("sv_table", C.c_void_p), ("sv_len", C.c_int32), ("sv_dt", C.c_double),
     ]
 
 
@@ -89,6 +90,8 @@ def lib():
         L.eo_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                   C.c_int64, C.c_void_p]
         L.eo_counters_get.argtypes = [C.c_void_p]
+        L.eo_set_departure_mode.restype = C.c_int32
+        L.eo_set_departure_mode.argtypes = [C.c_int32]
         L.eo_grad.restype = C.c_int
         L.eo_grad.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
                               C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -124,6 +127,12 @@ def _make_net(net: Network):
     if net.N0 is not None:
         keep.append(net.N0)
         s.N0 = _ptr(net.N0)
+    if getattr(net, "servers_schedule", None) is not None:
+        tab = np.ascontiguousarray(net.servers_schedule, dtype=np.int32)
+        keep.append(tab)
+        s.sv_table = _ptr(tab)
+        s.sv_len = tab.shape[0]
+        s.sv_dt = net.servers_schedule_dt
     return s, keep
 
 
@@ -181,6 +190,11 @@ def grad(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, rep_
     if scores:
         out["scores"] = sc
     return out
+
+
+def set_departure_mode(mode: int) -> int:
+    """0 exact (Algorithm 1), 1 Eq. (1), 2 Eq. (2); returns the previous mode."""
+    return int(lib().eo_set_departure_mode(mode))
 
 
 def set_cap(cap: int) -> int:

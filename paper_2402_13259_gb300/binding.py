@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libeulernet.so")
 
 BACKWARD, FORWARD = 0, 1
 (OPT_FORM, OPT_TILE_REPS, OPT_BLOCK, OPT_GRID, OPT_SAMPLER_CAP, OPT_GRAPH_STEPS, OPT_PIPE_WARPS,
- OPT_WAIT_LIMIT, OPT_TEST_STALL) = range(9)
+ OPT_WAIT_LIMIT, OPT_TEST_STALL, OPT_WAIT_SLEEP, OPT_DEPARTURE) = range(11)
 
 ERRORS = {
     -1: "EULER_ERR_ARG", -2: "EULER_ERR_NOT_FEEDFORWARD", -3: "EULER_ERR_CUDA", -4: "EULER_ERR_OOM",
@@ -90,6 +90,12 @@ def lib():
         L.euler_net_batch_simulate.restype = C.c_int
         L.euler_net_grad.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp, vp, vp, vp, vp]
         L.euler_net_grad.restype = C.c_int
+        L.euler_net_simulate_average.argtypes = [vp, dbl, dbl, i64, u64, i64, vp, vp, vp, vp]
+        L.euler_net_simulate_average.restype = C.c_int
+        L.euler_net_select_dt.argtypes = [vp, dbl]
+        L.euler_net_select_dt.restype = dbl
+        L.euler_net_set_servers_schedule.argtypes = [vp, vp, i32, dbl]
+        L.euler_net_set_servers_schedule.restype = C.c_int
         L.euler_net_h2d_bytes.argtypes = [vp]
         L.euler_net_h2d_bytes.restype = i64
         L.euler_net_destroy.argtypes = [vp]
@@ -158,6 +164,17 @@ class EulerNet:
         del keep
         _check(rc)
         self._h = h
+        if getattr(net, "servers_schedule", None) is not None:
+            self.set_servers_schedule(net.servers_schedule, net.servers_schedule_dt)
+
+    def set_servers_schedule(self, table, tab_dt: float):
+        """Staffing schedule m_i(t) = table[j, i] (see euler_net_set_servers_schedule);
+        table None clears it."""
+        if table is None:
+            _check(lib().euler_net_set_servers_schedule(self._h, None, 0, 1.0))
+            return
+        tab = np.ascontiguousarray(table, dtype=np.int32)
+        _check(lib().euler_net_set_servers_schedule(self._h, _ptr(tab), tab.shape[0], float(tab_dt)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -198,6 +215,26 @@ class EulerNet:
 
     def status(self, stream=None):
         _check(lib().euler_net_status(self._h, C.c_void_p(_stream_ptr(stream))))
+
+    def simulate_average(self, dt: float, T: float, R: int, seed: int, rep_begin: int = 0,
+                         stream=None, check: bool = True):
+        """Average scheme (both schemes on common random numbers): returns
+        (avg float64, backward int64, forward int64) device tensors."""
+        import torch
+        n = self.n
+        avg = torch.empty(stats_len(n, R), dtype=torch.float64, device="cuda")
+        sb = torch.empty(stats_len(n, R), dtype=torch.int64, device="cuda")
+        sf = torch.empty(stats_len(n, R), dtype=torch.int64, device="cuda")
+        _check(lib().euler_net_simulate_average(self._h, dt, T, R, seed, rep_begin,
+                                                C.c_void_p(avg.data_ptr()), C.c_void_p(sb.data_ptr()),
+                                                C.c_void_p(sf.data_ptr()),
+                                                C.c_void_p(_stream_ptr(stream))))
+        if check:
+            self.status(stream)
+        return avg, sb, sf
+
+    def select_dt(self, alpha: float = 0.0) -> float:
+        return float(lib().euler_net_select_dt(self._h, alpha))
 
     def grad(self, scheme: int, dt: float, T: float, R: int, seed: int, rep_begin: int = 0,
              scores: bool = False, stats: bool = False, stream=None, check: bool = True):

@@ -109,11 +109,35 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
   const int64_t K = euler_num_steps(dt, T);
   if (h->c_dt == dt && h->c_T == T) return EULER_OK;
   std::vector<float4> p0(h->n);
+  std::vector<float> muh(h->n);
   for (int32_t i = 0; i < h->n; ++i) {
     const float y = (float)(h->mu[i] * dt);
     const BinomConst bc = binom_const(-fm::expm1(-y));
     p0[i] = make_float4(bc.c0, bc.q, bc.r, bc.lq);
+    muh[i] = y;
   }
+  // servers of every step from the staffing schedule (value at the step's start)
+  if (h->sv_len > 0) {
+    std::vector<int32_t> mt((size_t)K * h->n);
+    for (int64_t tau = 1; tau <= K; ++tau) {
+      int64_t j = (int64_t)floor((double)(tau - 1) * dt / h->sv_dt);
+      if (j > h->sv_len - 1) j = h->sv_len - 1;
+      std::copy(h->sv_table.begin() + j * h->n, h->sv_table.begin() + (j + 1) * h->n,
+                mt.begin() + (tau - 1) * h->n);
+    }
+    if (mt.size() > h->mtab_cap || !h->d_mtab) {
+      cudaFree(h->d_mtab);
+      h->d_mtab = nullptr;
+      CUDA_TRY(cudaMalloc(&h->d_mtab, sizeof(int32_t) * mt.size()));
+      h->mtab_cap = mt.size();
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_mtab, mt.data(), sizeof(int32_t) * mt.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    h->h2d_bytes += (int64_t)(sizeof(int32_t) * mt.size());
+  }
+  if (!h->d_muh) CUDA_TRY(cudaMalloc(&h->d_muh, sizeof(float) * (size_t)h->n));
+  CUDA_TRY(cudaMemcpyAsync(h->d_muh, muh.data(), sizeof(float) * muh.size(), cudaMemcpyHostToDevice, s));
+  h->h2d_bytes += (int64_t)(sizeof(float) * muh.size());
   std::vector<float> lam((size_t)K * std::max(h->n_ex, 1), 0.0f);
   for (int32_t i = 0; i < h->n; ++i) {
     const int32_t c = h->ex_col[i];
@@ -393,6 +417,10 @@ void euler_net_destroy(euler_net* h) {
   cudaFree(h->d_gstats);
   cudaFree(h->d_gscores);
   cudaFree(h->d_gpartial);
+  cudaFree(h->d_avg_b);
+  cudaFree(h->d_avg_f);
+  cudaFree(h->d_mtab);
+  cudaFree(h->d_muh);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -526,8 +554,26 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
 
 int64_t euler_net_h2d_bytes(const euler_net* h) { return h ? h->h2d_bytes : -1; }
 
+int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t len, double tab_dt) {
+  if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
+  if (!table || len <= 0) {
+    h->sv_table.clear();
+    h->sv_len = 0;
+  } else {
+    if (!(tab_dt > 0.0) || !std::isfinite(tab_dt)) return fail(EULER_ERR_ARG, "schedule step must be finite and > 0");
+    for (int64_t k = 0; k < (int64_t)len * h->n; ++k)
+      if (table[k] < 1) return fail(EULER_ERR_ARG, "scheduled servers must be >= 1");
+    h->sv_table.assign(table, table + (int64_t)len * h->n);
+    h->sv_len = len;
+    h->sv_dt = tab_dt;
+  }
+  h->c_dt = h->c_T = -1.0;  // rebuild the per-step tables on the next call
+  h->g_dt = h->g_T = -1.0;
+  return EULER_OK;
+}
+
 int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
-  if (!h || option < 0 || option > EULER_OPT_TEST_STALL) return fail(EULER_ERR_ARG, "bad option");
+  if (!h || option < 0 || option > EULER_OPT_DEPARTURE) return fail(EULER_ERR_ARG, "bad option");
   h->opt[option] = value < 0 ? -1 : value;
   return EULER_OK;
 }
@@ -581,6 +627,10 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
   p.err = h->d_err;
   p.wait_limit = h->opt[EULER_OPT_WAIT_LIMIT] > 0 ? h->opt[EULER_OPT_WAIT_LIMIT] : (int64_t)1 << 25;
   p.test_stall = h->opt[EULER_OPT_TEST_STALL] > 0 ? 1 : 0;
+  p.wait_sleep_ns = h->opt[EULER_OPT_WAIT_SLEEP] >= 0 ? (int32_t)std::min<int64_t>(h->opt[EULER_OPT_WAIT_SLEEP], 1000000) : 64;
+  p.muh = h->d_muh;
+  p.dep_mode = h->dep_mode();
+  p.mtab = h->mtab();
   const NetTables t = h->tables();
   if (pl.form == 3) {
     cudaError_t e = launch_pipeline(t, p, pl.pipe, pl.grid, (int)pl.smem, s);
@@ -663,6 +713,7 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
   if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return fail(EULER_ERR_ARG, "unknown scheme");
   if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T)) return fail(EULER_ERR_ARG, "dt and T must be finite and > 0");
   if (R < 1 || rep_begin < 0 || !grad || !value) return fail(EULER_ERR_ARG, "bad replications, rep_begin, grad or value");
+  if (h->dep_mode() != 0) return fail(EULER_ERR_ARG, "gradients need the exact departure sampler (EULER_OPT_DEPARTURE = 0)");
   if (rep_begin + R > (int64_t)1 << 32) return fail(EULER_ERR_TOO_LARGE, "replication index beyond 2^32");
   const int64_t K = euler_num_steps(dt, T);
   if (K >= (1 << 24)) return fail(EULER_ERR_TOO_LARGE, "too many steps (T/dt >= 2^24)");
@@ -727,12 +778,54 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
   p.p0f = h->d_p0f;
   p.dlam = h->d_dlam;
   p.scores = scores;
+  p.muh = h->d_muh;
+  p.dep_mode = 0;
+  p.mtab = h->mtab();
   CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s));
   e = launch_persistent_grad(h->tables(), p, grid, block, (int)smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
   e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var, s);
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
   return EULER_OK;
+}
+
+int euler_net_simulate_average(euler_net* h, double dt, double T, int64_t R, uint64_t seed,
+                               int64_t rep_begin, double* stats_avg, int64_t* stats_b,
+                               int64_t* stats_f, void* stream) {
+  if (!h || !stats_avg || R < 0) return fail(EULER_ERR_ARG, "bad average-scheme arguments");
+  const size_t len = (size_t)euler_stats_len(h->n, R);
+  if (!stats_b || !stats_f) {
+    if (len > h->avg_cap || !h->d_avg_b) {
+      cudaFree(h->d_avg_b);
+      cudaFree(h->d_avg_f);
+      h->d_avg_b = h->d_avg_f = nullptr;
+      CUDA_TRY(cudaMalloc(&h->d_avg_b, sizeof(int64_t) * std::max<size_t>(len, 1)));
+      CUDA_TRY(cudaMalloc(&h->d_avg_f, sizeof(int64_t) * std::max<size_t>(len, 1)));
+      h->avg_cap = len;
+    }
+    if (!stats_b) stats_b = h->d_avg_b;
+    if (!stats_f) stats_f = h->d_avg_f;
+  }
+  int rc = euler_net_simulate(h, EULER_BACKWARD, dt, T, R, seed, rep_begin, stats_b, stream);
+  if (rc) return rc;
+  rc = euler_net_simulate(h, EULER_FORWARD, dt, T, R, seed, rep_begin, stats_f, stream);
+  if (rc) return rc;
+  cudaError_t e = launch_average(stats_b, stats_f, stats_avg, (int64_t)len,
+                                 reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "average kernel launch");
+  return EULER_OK;
+}
+
+double euler_net_select_dt(const euler_net* h, double alpha) {
+  if (!h) return -1.0;
+  double mu_max = 0.0;
+  int32_t m_max = 1;
+  for (int32_t i = 0; i < h->n; ++i) {
+    mu_max = std::max(mu_max, h->mu[i]);
+    m_max = std::max(m_max, h->servers[i]);
+  }
+  if (!(alpha > 0.0)) alpha = 0.4 / std::sqrt((double)m_max);
+  return alpha / mu_max;
 }
 
 int euler_net_status(euler_net* h, void* stream) {

@@ -136,6 +136,9 @@ int make_batch_plan(euler_batch* b, int block, int64_t cap) {
     p.wait_limit = (int64_t)1 << 25;
     p.test_stall = 0;
     p.sacc_in_global = sacc_global ? 1 : 0;
+    p.muh = h->d_muh;
+    p.dep_mode = h->dep_mode();
+    p.mtab = h->mtab();
     b->h_runs[j] = p;
     b->h_nets[j] = h->tables();
     const double c = (double)h->n * (double)K * (double)Rt;

@@ -26,6 +26,14 @@ struct euler_net {
   float* d_mu = nullptr;
   unsigned* d_err = nullptr;
 
+  // staffing schedule (host copy) and its per-step table
+  std::vector<int32_t> sv_table;
+  int32_t sv_len = 0;
+  double sv_dt = 1.0;
+  int32_t* d_mtab = nullptr;
+  size_t mtab_cap = 0;
+  float* d_muh = nullptr;
+
   // per-(dt, T) tables of the last call
   double c_dt = -1.0, c_T = -1.0;
   int32_t c_K = 0;
@@ -45,14 +53,22 @@ struct euler_net {
   double* d_gpartial = nullptr;
   size_t gpartial_cap = 0;
 
+  // scratch of the average scheme
+  int64_t* d_avg_b = nullptr;
+  int64_t* d_avg_f = nullptr;
+  size_t avg_cap = 0;
+
   // HBM-form state
   int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr;
   int64_t* d_racc = nullptr;
   int64_t hbm_cap_ld = 0, hbm_cap_R = 0;
   cudaStream_t cap_stream = nullptr;
 
-  int64_t opt[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+  int64_t opt[11] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
   int64_t h2d_bytes = 0;  // host-to-device bytes copied by this handle so far
+
+  int32_t dep_mode() const { return opt[EULER_OPT_DEPARTURE] > 0 ? (int32_t)opt[EULER_OPT_DEPARTURE] : 0; }
+  const int32_t* mtab() const { return sv_len > 0 ? d_mtab : nullptr; }
 
   eulernet::NetTables tables() const {
     eulernet::NetTables t;

@@ -41,8 +41,12 @@ struct RunParams {
   int64_t num_tiles;
   int32_t cap;        // rejection-loop cap
   int64_t wait_limit; // polls of one inter-warp wait before it gives up (pipelined form)
+  int32_t wait_sleep_ns; // pause between polls (pipelined form), 0 = none
   int32_t test_stall; // nonzero: no warp publishes progress (tests the timeout path)
   int32_t sacc_in_global;  // batch kernel: per-station sums in the global scratch slot
+  const float* muh;      // [n] mu_i dt rounded to float (Eq. (1)/(2) departures)
+  int32_t dep_mode;      // 0 exact (Algorithm 1), 1 Eq. (1), 2 Eq. (2)
+  const int32_t* mtab;   // [K][n] servers per step (staffing schedule), or nullptr
   // likelihood-ratio gradients (persistent form, GRAD kernels only)
   const float* p0f;   // [n] p0 as the sampler uses it
   const float* dlam;  // [K][n_ex][3] dLambda/d(a, b, phase)
@@ -69,6 +73,10 @@ cudaError_t launch_persistent_grad(const NetTables& t, const RunParams& p, int g
 cudaError_t launch_grad_reduce(int32_t n, int64_t R, double dt, const int64_t* stats,
                                const double* scores, double* partial, double* grad, double* value,
                                double* grad_var, cudaStream_t s);
+
+// out[k] = (b[k] + f[k]) / 2 in double.
+cudaError_t launch_average(const int64_t* b, const int64_t* f, double* out, int64_t len,
+                           cudaStream_t s);
 
 // Launch the persistent shared-memory kernel.
 cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block,

@@ -160,7 +160,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
           int32_t v[2] = {0, 0};
           if (act) {
             const int32_t nn = backward_gather(t, su, Ns, Rs, Rt, r, cx.err);
-            const int32_t c = __ldg(t.servers + su);
+            const int32_t c = servers_at(t, p, su, (uint32_t)tau);
             v[0] = nn;
             v[1] = nn < c ? nn : c;
             q_r += nn;
@@ -181,7 +181,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
             if (act) {
               const UnitOut o = unit_update<true, GRAD>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
               if (GRAD) add_scores(t, p, sm, i, tau, r, Rt, o);
-              const int32_t c = __ldg(t.servers + i);
+              const int32_t c = servers_at(t, p, i, (uint32_t)tau);
               v[0] = o.N;
               v[1] = o.N < c ? o.N : c;
               v[2] = o.D;
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParam
     int32_t v[2] = {0, 0};
     if (act) {
       const int32_t nn = backward_gather(t, i, hs.N, hs.Redge, hs.ld, rloc, cx.err);
-      const int32_t c = __ldg(t.servers + i);
+      const int32_t c = servers_at(t, p, i, (uint32_t)tau);
       v[0] = nn; v[1] = nn < c ? nn : c;
       part[0] = nn;
     }
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParam
     int32_t v[5] = {0, 0, 0, 0, 0};
     if (act) {
       const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
-      const int32_t c = __ldg(t.servers + i);
+      const int32_t c = servers_at(t, p, i, (uint32_t)tau);
       v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
       part[0] = o.N; part[1] = o.D; part[2] = o.X; part[3] = o.A;
     }
@@ -587,6 +587,20 @@ cudaError_t launch_grad_reduce(int32_t n, int64_t R, double dt, const int64_t* s
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   grad_final_kernel<<<8, 128, 0, s>>>(n, R, nb, partial, grad, value, grad_var);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void average_kernel(const int64_t* b, const int64_t* f, double* out, int64_t len) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = 0.5 * ((double)b[k] + (double)f[k]);
+}
+}  // namespace
+
+cudaError_t launch_average(const int64_t* b, const int64_t* f, double* out, int64_t len,
+                           cudaStream_t s) {
+  average_kernel<<<256, 256, 0, s>>>(b, f, out, len);
   return cudaGetLastError();
 }
 

@@ -84,12 +84,17 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   if (K >= (1 << 24)) return noalloc_fail(EULER_ERR_TOO_LARGE, "too many steps (T/dt >= 2^24)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
 
-  // scratch layout: [err, tau] | p0 constants[n] | lam[K][n_ex] | racc[R][4] | N[n][ld] | Redge[E][ld]
+  // scratch layout: [err, tau] | p0 constants[n] | mu h[n] | servers[K][n] (schedule only) |
+  //                 lam[K][n_ex] | racc[R][4] | N[n][ld] | Redge[E][ld]
   const int64_t ld = (R + 3) / 4 * 4;
   const int64_t n_ex = h->n_ex > 0 ? h->n_ex : 1;
   size_t off = 256;
   const size_t off_p0 = off;
   off = align256(off + sizeof(float4) * (size_t)h->n);
+  const size_t off_muh = off;
+  off = align256(off + sizeof(float) * (size_t)h->n);
+  const size_t off_mtab = off;
+  if (h->sv_len > 0) off = align256(off + sizeof(int32_t) * (size_t)K * (size_t)h->n);
   const size_t off_lam = off;
   off = align256(off + sizeof(float) * (size_t)K * (size_t)n_ex);
   const size_t off_racc = off;
@@ -127,6 +132,25 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
     }
     e = cudaMemcpyAsync(d_p0 + i0, g_stage, sizeof(float4) * cnt, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // staging buffer is reused
+  }
+  float* d_muh = reinterpret_cast<float*>(base + off_muh);
+  for (int32_t i0 = 0; i0 < h->n && e == cudaSuccess; i0 += kStage) {
+    const int32_t cnt = h->n - i0 < kStage ? h->n - i0 : kStage;
+    for (int32_t k = 0; k < cnt; ++k) g_stage[k] = (float)(h->mu[i0 + k] * dt);
+    e = cudaMemcpyAsync(d_muh + i0, g_stage, sizeof(float) * cnt, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // staging buffer is reused
+  }
+  int32_t* d_mtab = nullptr;
+  if (h->sv_len > 0) {
+    d_mtab = reinterpret_cast<int32_t*>(base + off_mtab);
+    // one step's row at a time, straight from the schedule (no staging needed)
+    for (int64_t tau = 1; tau <= K && e == cudaSuccess; ++tau) {
+      int64_t j = (int64_t)floor((double)(tau - 1) * dt / h->sv_dt);
+      if (j > h->sv_len - 1) j = h->sv_len - 1;
+      e = cudaMemcpyAsync(d_mtab + (tau - 1) * h->n, h->sv_table.data() + j * h->n,
+                          sizeof(int32_t) * (size_t)h->n, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   if (h->n_ex > 0) {
     const int64_t total = K * h->n_ex;
@@ -170,6 +194,9 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   p.err = d_err;
   p.wait_limit = (int64_t)1 << 25;
   p.test_stall = 0;
+  p.muh = d_muh;
+  p.dep_mode = h->dep_mode();
+  p.mtab = d_mtab;
   HbmState hs;
   hs.tau = reinterpret_cast<int32_t*>(base + 4);
   hs.racc = reinterpret_cast<int64_t*>(base + off_racc);

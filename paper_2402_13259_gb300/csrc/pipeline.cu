@@ -51,7 +51,8 @@ __device__ __forceinline__ void publish(int* ctr, int w, int tau, bool mute) {
 
 // Wait until ctr[b] >= need for every warp b in `mask`, at most `limit` polls
 // per warp waited on.
-__device__ __forceinline__ bool wait_mask(int* ctr, unsigned mask, int need, long long limit) {
+__device__ __forceinline__ bool wait_mask(int* ctr, unsigned mask, int need, long long limit,
+                                          int sleep_ns) {
   int ok = 1;
   if (mask != 0u && need > 0 && (threadIdx.x & 31) == 0) {
     unsigned m = mask;
@@ -64,7 +65,7 @@ __device__ __forceinline__ bool wait_mask(int* ctr, unsigned mask, int need, lon
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (sleep_ns > 0) __nanosleep(sleep_ns);
       }
     }
   }
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(512, 2) pipeline_kernel(NetTables t, RunParams
   const unsigned prod = pp.prod[w], cons = pp.cons[w];
   const bool lead = lane == 0;
   const long long lim = p.wait_limit;
+  const int zz = p.wait_sleep_ns;
   const bool mute = p.test_stall != 0;
 
   for (int k = tid; k < 64; k += nthr) rinv[k] = k ? 1.0f / (float)k : 0.0f;
@@ -116,16 +118,16 @@ __global__ void __launch_bounds__(512, 2) pipeline_kernel(NetTables t, RunParams
     for (int32_t tau = 1; tau <= p.K && ok; ++tau) {
       const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
       int32_t* slot = Rs + (tau & 1) * slot_stride;
-      ok = wait_mask(done, cons, tau - 2, lim);  // the buffer this step writes is free
+      ok = wait_mask(done, cons, tau - 2, lim, zz);  // the buffer this step writes is free
       if (SCHEME == 1) {
-        ok = ok && wait_mask(ph1, prod, tau, lim);  // upstream routed counts of this step
+        ok = ok && wait_mask(ph1, prod, tau, lim, zz);  // upstream routed counts of this step
         for (int k = k_begin; k < k_end; ++k) {
           const int32_t i = __ldg(t.lvl_station + k);
           int32_t v[5] = {0, 0, 0, 0, 0};
           if (rvalid) {
             const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, slot,
                                                 kPipeTile, lane, cx);
-            const int32_t c = __ldg(t.servers + i);
+            const int32_t c = servers_at(t, p, i, (uint32_t)tau);
             v[0] = o.N;
             v[1] = o.N < c ? o.N : c;
             v[2] = o.D;
@@ -157,13 +159,13 @@ __global__ void __launch_bounds__(512, 2) pipeline_kernel(NetTables t, RunParams
           reduce_to<3>(sacc + 6 * (int64_t)i + 2, v, lead, 32, false);
         }
         publish(ph1, w, tau, mute);
-        ok = ok && wait_mask(ph1, prod, tau, lim);
+        ok = ok && wait_mask(ph1, prod, tau, lim, zz);
         for (int k = k_begin; k < k_end; ++k) {
           const int32_t i = __ldg(t.lvl_station + k);
           int32_t v[2] = {0, 0};
           if (rvalid) {
             const int32_t nn = backward_gather(t, i, Ns, slot, kPipeTile, lane, cx.err);
-            const int32_t c = __ldg(t.servers + i);
+            const int32_t c = servers_at(t, p, i, (uint32_t)tau);
             v[0] = nn;
             v[1] = nn < c ? nn : c;
             q_r += nn;

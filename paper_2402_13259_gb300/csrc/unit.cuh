@@ -16,6 +16,13 @@ __device__ __forceinline__ void latch(unsigned* err, unsigned bits) {
 
 __device__ __forceinline__ BinomConst as_const(float4 v) { return BinomConst{v.x, v.y, v.z, v.w}; }
 
+// Servers of station i during step tau (a staffing schedule, Sec. 2.1.2, or
+// the constant m_i).
+__device__ __forceinline__ int32_t servers_at(const NetTables& t, const RunParams& p, int32_t i,
+                                              uint32_t tau) {
+  return p.mtab ? __ldg(p.mtab + (int64_t)(tau - 1) * t.n + i) : __ldg(t.servers + i);
+}
+
 __device__ __forceinline__ int64_t gather_in(const NetTables& t, int32_t i, const int32_t* redge,
                                              int64_t stride, int64_t col) {
   int64_t s = 0;
@@ -88,13 +95,24 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
                                                 SamplerCtx& cx, int32_t& D, int32_t& X, float& smu) {
   PhiloxStream svc;
   svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
-  const BinomialArgs dep = departure_branch(y, __ldg(t.servers + i), __ldg(t.mu + i), p.h,
-                                            as_const(__ldg(p.p0 + i)), svc, cx);
+  const int32_t m = servers_at(t, p, i, tau);
   const int32_t e0 = __ldg(t.row_ptr + i);
   const int32_t deg = __ldg(t.row_ptr + i + 1) - e0;
   int32_t rem = 0;
+  int32_t j0 = -1;
   D = 0;
-  for (int32_t j = -1; j < deg; ++j) {
+  BinomialArgs dep;
+  if (p.dep_mode == 1 || (p.dep_mode == 2 && y > m)) {
+    // Eq. (1) (Eq. (2) for x > m): D = min(x, Poisson(min(x, m) mu h))
+    const int32_t b = y < m ? y : m;
+    const int32_t S = poisson((float)b * __ldg(p.muh + i), svc, cx);
+    D = S < y ? S : y;
+    rem = D;
+    j0 = 0;
+  } else {
+    dep = departure_branch(y, m, __ldg(t.mu + i), p.h, as_const(__ldg(p.p0 + i)), svc, cx);
+  }
+  for (int32_t j = j0; j < deg; ++j) {
     const int32_t nb = j < 0 ? dep.n : rem;
     const BinomConst bc = j < 0 ? dep.c : as_const(__ldg(t.qc + e0 + j));
     const int32_t v = binomial_c(nb, bc, svc, cx);  // Bin(0, .) draws nothing
@@ -106,7 +124,6 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
         //   x <= m : Bin(x, p0(mu)), dp0/dmu = h(1 - p0)        -> h (k/p0 - x)
         //   x >  m : Erlang(x - m, m mu) density at T            -> (x - m)/mu - m T
         //            plus, if T <= h, Bin(m, p(mu)), dp/dmu = (h - T)(1 - p) -> (h - T)(k/p - m)
-        const int32_t m = __ldg(t.servers + i);
         if (dep.branch == 0) {
           smu = p.h * ((v > 0 ? (float)v / __ldg(p.p0f + i) : 0.0f) - (float)y);
         } else {

@@ -70,6 +70,10 @@ class Network:
     arrivals: Arrivals
     N0: Optional[np.ndarray] = None  # int32 [n]
     layer: Optional[np.ndarray] = None  # int32 [n], generator's layer index
+    # optional staffing schedule m_i(t) = servers_schedule[j, i],
+    # j = min(floor(t / servers_schedule_dt), J - 1)
+    servers_schedule: Optional[np.ndarray] = None  # int32 [J, n]
+    servers_schedule_dt: float = 1.0
 
     def __post_init__(self):
         self.row_ptr = np.ascontiguousarray(self.row_ptr, dtype=np.int32)

@@ -568,3 +568,96 @@ def test_gradient_matches_infinite_server_closed_form(orc, scheme):
     se = np.sqrt(g["var"])
     z = (g["grad"] - want) / np.maximum(se, 1e-12)
     assert np.abs(z).max() < 5.0, z
+
+
+# ---------------------------------------------------------------------------
+# Average scheme (Sec. 7.1) and step-size rule (Sec. 5.4)
+# ---------------------------------------------------------------------------
+def test_average_scheme_second_order_on_infinite_server(orc):
+    """M/M/inf station: the backward and forward steady states are
+    lambda h / (1 - e^{-mu h}) and e^{-mu h} times that (derived from Lemma
+    1(1) and the schemes' updates); their average is (lambda/mu)(mu h/2)
+    coth(mu h/2) = (lambda/mu)(1 + (mu h)^2/12 + ...), so halving h cuts the
+    average's error about four-fold and each scheme's two-fold -- the slope-2
+    observation of Sec. 7.3.  The oracle's long-run means follow these forms."""
+    lam, mu, R, burn = 40.0, 1.0, 400, 200
+    res = {}
+    for h in (0.5, 0.25):
+        K = int(round(400 / h))
+        run = W.single_station(1_000_000, mu, lam, h, K * h, R, 5, N0=40)
+        nb = orc.simulate(run.net, 0, h, K * h, R, 5, trace=True)["N"][burn:, 0, :].mean()
+        nf = orc.simulate(run.net, 1, h, K * h, R, 5, trace=True)["N"][burn:, 0, :].mean()
+        eb = lam * h / (1 - math.exp(-mu * h))
+        ef = eb * math.exp(-mu * h)
+        assert abs(nb - eb) < 0.01 * eb and abs(nf - ef) < 0.01 * ef
+        res[h] = ((nb + nf) / 2 - lam / mu, nb - lam / mu)
+    (avg1, b1), (avg2, b2) = res[0.5], res[0.25]
+    assert 3.0 < avg1 / avg2 < 5.5, (avg1, avg2)
+    assert 1.7 < b1 / b2 < 2.3, (b1, b2)
+
+
+# ---------------------------------------------------------------------------
+# Simpler departure samplers, Eq. (1) and Eq. (2) of Sec. 3.1
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("x,m,mu,h", [(4, 6, 1.0, 0.5), (12, 3, 2.0, 0.5), (30, 8, 0.5, 2.0)])
+def test_naive_departure_laws(orc, x, m, mu, h):
+    """Eq. (1): D = min(x, Poisson(min(x, m) mu h)); Eq. (2): binomial law of
+    Lemma 1(1) for x <= m, Eq. (1) otherwise.  Both over-estimate E[D]
+    against the exact law exp(Q h) (the remark after Eq. (1))."""
+    N = 300_000
+    b = min(x, m)
+    lam = float(np.float32(b * float(np.float32(mu * h))))
+    pois = stats.poisson.pmf(np.arange(x + 1), lam)
+    pois[x] = stats.poisson.sf(x - 1, lam)
+    exact = _pure_death_law(x, m, float(np.float32(mu)), float(np.float32(h)))
+    old = orc.set_departure_mode(1)
+    try:
+        d1 = orc.draw_departure(x, m, mu, h, 77, N)
+        orc.set_departure_mode(2)
+        d2 = orc.draw_departure(x, m, mu, h, 78, N)
+    finally:
+        orc.set_departure_mode(old)
+    assert _chi2_p(np.bincount(d1, minlength=x + 1), pois * N) > 1e-4
+    law2 = exact if x <= m else pois
+    if x <= m:
+        p0 = float(np.float32(-np.expm1(-np.float32(mu * h))))
+        law2 = stats.binom.pmf(np.arange(x + 1), x, p0)
+    assert _chi2_p(np.bincount(d2, minlength=x + 1), law2 * N) > 1e-4
+    e_exact = (exact * np.arange(x + 1)).sum()
+    e_naive = (pois * np.arange(x + 1)).sum()
+    assert e_naive >= e_exact - 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Time-varying staffing (Sec. 2.1.2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_staffing_schedule_exact_distribution(orc, scheme):
+    """With a staffing schedule each step's pure-departure law uses that step's
+    servers: the single-station distribution propagated exactly with the
+    scheduled m (brute force) matches the oracle; a constant schedule changes
+    nothing."""
+    mu, lam, h, N0, K = 1.0, 3.0, 0.5, 2, 6
+    sched = np.array([[1], [4], [2], [4]], dtype=np.int32)  # m over [0,1), [1,2), [2,3), [3, inf)
+    run = W.single_station(4, mu, lam, h, K * h, 200_000, 43, N0=N0)
+    net = run.net
+    net.servers_schedule, net.servers_schedule_dt = sched, 1.0
+    res = orc.simulate(net, scheme, h, K * h, run.R, run.seed, trace=True)
+    smax = 90
+    a = stats.poisson.pmf(np.arange(smax + 1), lam * h)
+    P = np.zeros(smax + 1)
+    P[N0] = 1.0
+    for t in range(K):
+        m = int(sched[min(int((t * h) // 1.0), 3), 0])
+        G = np.zeros((smax + 1, smax + 1))
+        for x in range(smax + 1):
+            law = _pure_death_law(x, m, float(np.float32(mu)), float(np.float32(h)))
+            G[x, x - np.arange(x + 1)] = law
+        P = np.convolve(P @ G, a)[: smax + 1] if scheme == 0 else np.convolve(P, a)[: smax + 1] @ G
+        obs = np.bincount(res["N"][t, 0], minlength=smax + 1)[: smax + 1]
+        assert _chi2_p(obs, P * run.R) > 1e-4
+    # a constant schedule equal to the servers is the same run
+    net2 = W.single_station(4, mu, lam, h, K * h, 500, 43, N0=N0).net
+    base = orc.simulate(net2, scheme, h, K * h, 500, 43)["stats"]
+    net2.servers_schedule, net2.servers_schedule_dt = np.array([[4]], dtype=np.int32), 1.0
+    assert np.array_equal(orc.simulate(net2, scheme, h, K * h, 500, 43)["stats"], base)
