@@ -206,10 +206,12 @@ cudaError_t enqueue(euler_batch* b, int64_t* const* stats, cudaStream_t s) {
   for (int j = 0; j < b->count && e == cudaSuccess; ++j)
     e = cudaMemsetAsync(stats[j], 0,
                         sizeof(int64_t) * (size_t)euler_stats_len(b->nets[j]->n, b->runs[j].replications), s);
+  bool ext = false;
+  for (const RunParams& rp : b->h_runs) ext = ext || rp.mtab != nullptr || rp.dep_mode != 0;
   int off = 0;
   for (int sc = 0; sc < 2 && e == cudaSuccess; ++sc) {
     if (b->num_items_s[sc] > 0)
-      e = launch_batch(sc, b->d_nets, b->d_runs, b->d_items + off, b->num_items_s[sc], b->d_counter + sc,
+      e = launch_batch(sc, ext, b->d_nets, b->d_runs, b->d_items + off, b->num_items_s[sc], b->d_counter + sc,
                        b->d_sacc, b->sacc_slot_len, b->grid, b->block, b->smem, s);
     off += b->num_items_s[sc];
   }

@@ -60,7 +60,7 @@ int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps);
 
 // Batched form: one persistent launch over (network, tile) work items.
 cudaError_t batch_occupancy(int block, int smem, int* blocks_per_sm);
-cudaError_t launch_batch(int scheme, const NetTables* nets, const RunParams* runs, const int2* items,
+cudaError_t launch_batch(int scheme, bool ext, const NetTables* nets, const RunParams* runs, const int2* items,
                          int num_items, int* next_item, long long* sacc_scratch,
                          int64_t sacc_slot_len, int grid, int block, int smem, cudaStream_t s);
 

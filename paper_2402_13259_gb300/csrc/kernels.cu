@@ -78,7 +78,7 @@ __device__ __forceinline__ void add_scores(const NetTables& t, const RunParams& 
 // One tile: the whole time loop for replications tile*Rt ... of network t.
 // Adds per-station sums (and N_K) into sm.sacc and writes the tile's
 // per-replication sums to p.stats.  Ends with a block barrier.
-template <int SCHEME, bool GRAD = false>
+template <int SCHEME, bool GRAD = false, bool EXT = true>
 __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p, int64_t tile,
                                           const TileSmem& sm, SamplerCtx& cx) {
   const int32_t n = t.n;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
           const bool act = rvalid && su < n;
           int32_t v[3] = {0, 0, 0};
           if (act) {
-            const UnitOut o = unit_update<false, GRAD>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+            const UnitOut o = unit_update<false, GRAD, EXT>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
             if (GRAD) add_scores(t, p, sm, su, tau, r, Rt, o);
             v[0] = o.D;
             v[1] = o.X;
@@ -160,7 +160,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
           int32_t v[2] = {0, 0};
           if (act) {
             const int32_t nn = backward_gather(t, su, Ns, Rs, Rt, r, cx.err);
-            const int32_t c = servers_at(t, p, su, (uint32_t)tau);
+            const int32_t c = servers_at<EXT>(t, p, su, (uint32_t)tau);
             v[0] = nn;
             v[1] = nn < c ? nn : c;
             q_r += nn;
@@ -179,9 +179,9 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
             const int32_t i = su < m ? __ldg(t.lvl_station + s0 + su) : 0;
             int32_t v[5] = {0, 0, 0, 0, 0};
             if (act) {
-              const UnitOut o = unit_update<true, GRAD>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+              const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
               if (GRAD) add_scores(t, p, sm, i, tau, r, Rt, o);
-              const int32_t c = servers_at(t, p, i, (uint32_t)tau);
+              const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
               v[0] = o.N;
               v[1] = o.N < c ? o.N : c;
               v[2] = o.D;
@@ -240,7 +240,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
 }
 
 // Single network: CTAs loop over the tiles.
-template <int SCHEME, bool GRAD = false>
+template <int SCHEME, bool GRAD = false, bool EXT = true>
 __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int claim[2];
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunPara
   SamplerCtx cx{sm.rinv, p.cap, 0u};
   __syncthreads();
   for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
-    tile_body<SCHEME, GRAD>(t, p, tile, sm, cx);
+    tile_body<SCHEME, GRAD, EXT>(t, p, tile, sm, cx);
   flush_station_sums(t, p, sm.sacc);
   latch(p.err, cx.err);
 }
@@ -336,7 +336,7 @@ __global__ void grad_final_kernel(int32_t n, int64_t R, int64_t nb, const double
 // size, scheme, stats buffer); per-station sums go to shared memory when the
 // network's layout fits (runs[j].sacc_slot < 0) or to the CTA's slot of a
 // global scratch array otherwise.
-template <int SCHEME>
+template <int SCHEME, bool EXT>
 __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, const RunParams* runs,
                                                        const int2* items, int num_items,
                                                        int* next_item, long long* sacc_scratch,
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
     sm.claim = claim;
     for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sm.sacc[k] = 0;
     __syncthreads();
-    tile_body<SCHEME>(t, p, wi.y, sm, cx);
+    tile_body<SCHEME, false, EXT>(t, p, wi.y, sm, cx);
     flush_station_sums(t, p, sm.sacc);
     __syncthreads();
     err |= cx.err;
@@ -512,48 +512,65 @@ int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps) {
          4 * ((int64_t)n + E) * tile_reps;
 }
 
-cudaError_t persistent_occupancy(int scheme, int block, int smem, int* blocks_per_sm) {
-  const void* fn = scheme == 0 ? (const void*)persistent_kernel<0> : (const void*)persistent_kernel<1>;
+namespace {
+bool uses_ext(const RunParams& p) { return p.mtab != nullptr || p.dep_mode != 0; }
+
+template <bool GRAD>
+const void* persistent_fn(int scheme, bool ext) {
+  if (scheme == 0)
+    return ext ? (const void*)persistent_kernel<0, GRAD, true> : (const void*)persistent_kernel<0, GRAD, false>;
+  return ext ? (const void*)persistent_kernel<1, GRAD, true> : (const void*)persistent_kernel<1, GRAD, false>;
+}
+
+const void* batch_fn(int scheme, bool ext) {
+  if (scheme == 0) return ext ? (const void*)batch_kernel<0, true> : (const void*)batch_kernel<0, false>;
+  return ext ? (const void*)batch_kernel<1, true> : (const void*)batch_kernel<1, false>;
+}
+
+// Occupancy of the tightest of a set of instantiations at (block, smem).
+cudaError_t min_occupancy(const void* const* fns, int count, int block, int smem, int* blocks_per_sm) {
+  int best = 1 << 30;
+  for (int k = 0; k < count; ++k) {
+    cudaError_t e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int v = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fns[k], block, smem);
+    if (e != cudaSuccess) return e;
+    best = v < best ? v : best;
+  }
+  *blocks_per_sm = best;
+  return cudaSuccess;
+}
+
+cudaError_t launch_fn(const void* fn, void** args, int grid, int block, int smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)smem, s);
+}
+}  // namespace
+
+cudaError_t persistent_occupancy(int scheme, int block, int smem, int* blocks_per_sm) {
+  const void* fns[2] = {persistent_fn<false>(scheme, false), persistent_fn<false>(scheme, true)};
+  return min_occupancy(fns, 2, block, smem, blocks_per_sm);
 }
 
 cudaError_t launch_persistent(const NetTables& t, const RunParams& p, int grid, int block, int smem,
                               cudaStream_t s) {
-  const void* fn = p.scheme == 0 ? (const void*)persistent_kernel<0> : (const void*)persistent_kernel<1>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  if (p.scheme == 0)
-    persistent_kernel<0><<<grid, block, smem, s>>>(t, p);
-  else
-    persistent_kernel<1><<<grid, block, smem, s>>>(t, p);
-  return cudaGetLastError();
+  NetTables tt = t;
+  RunParams pp = p;
+  void* args[] = {&tt, &pp};
+  return launch_fn(persistent_fn<false>(p.scheme, uses_ext(p)), args, grid, block, smem, s);
 }
 
 cudaError_t batch_occupancy(int block, int smem, int* blocks_per_sm) {
-  int a = 0, b = 0;
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<0>, block, smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel<1>, block, smem);
-  *blocks_per_sm = a < b ? a : b;
-  return e;
+  const void* fns[4] = {batch_fn(0, false), batch_fn(1, false), batch_fn(0, true), batch_fn(1, true)};
+  return min_occupancy(fns, 4, block, smem, blocks_per_sm);
 }
 
-cudaError_t launch_batch(int scheme, const NetTables* nets, const RunParams* runs, const int2* items,
-                         int num_items, int* next_item, long long* sacc_scratch,
+cudaError_t launch_batch(int scheme, bool ext, const NetTables* nets, const RunParams* runs,
+                         const int2* items, int num_items, int* next_item, long long* sacc_scratch,
                          int64_t sacc_slot_len, int grid, int block, int smem, cudaStream_t s) {
-  const void* fn = scheme == 0 ? (const void*)batch_kernel<0> : (const void*)batch_kernel<1>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  if (scheme == 0)
-    batch_kernel<0><<<grid, block, smem, s>>>(nets, runs, items, num_items, next_item, sacc_scratch,
-                                              sacc_slot_len);
-  else
-    batch_kernel<1><<<grid, block, smem, s>>>(nets, runs, items, num_items, next_item, sacc_scratch,
-                                              sacc_slot_len);
-  return cudaGetLastError();
+  void* args[] = {&nets, &runs, &items, &num_items, &next_item, &sacc_scratch, &sacc_slot_len};
+  return launch_fn(batch_fn(scheme, ext), args, grid, block, smem, s);
 }
 
 int64_t grad_smem_extra(int32_t n, int32_t n_ex, int32_t tile_reps) {
@@ -561,22 +578,16 @@ int64_t grad_smem_extra(int32_t n, int32_t n_ex, int32_t tile_reps) {
 }
 
 cudaError_t grad_occupancy(int scheme, int block, int smem, int* blocks_per_sm) {
-  const void* fn = scheme == 0 ? (const void*)persistent_kernel<0, true> : (const void*)persistent_kernel<1, true>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+  const void* fns[2] = {persistent_fn<true>(scheme, false), persistent_fn<true>(scheme, true)};
+  return min_occupancy(fns, 2, block, smem, blocks_per_sm);
 }
 
 cudaError_t launch_persistent_grad(const NetTables& t, const RunParams& p, int grid, int block,
                                    int smem, cudaStream_t s) {
-  const void* fn = p.scheme == 0 ? (const void*)persistent_kernel<0, true> : (const void*)persistent_kernel<1, true>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  if (p.scheme == 0)
-    persistent_kernel<0, true><<<grid, block, smem, s>>>(t, p);
-  else
-    persistent_kernel<1, true><<<grid, block, smem, s>>>(t, p);
-  return cudaGetLastError();
+  NetTables tt = t;
+  RunParams pp = p;
+  void* args[] = {&tt, &pp};
+  return launch_fn(persistent_fn<true>(p.scheme, uses_ext(p)), args, grid, block, smem, s);
 }
 
 cudaError_t launch_grad_reduce(int32_t n, int64_t R, double dt, const int64_t* stats,

@@ -18,9 +18,11 @@ __device__ __forceinline__ BinomConst as_const(float4 v) { return BinomConst{v.x
 
 // Servers of station i during step tau (a staffing schedule, Sec. 2.1.2, or
 // the constant m_i).
+template <bool EXT = true>
 __device__ __forceinline__ int32_t servers_at(const NetTables& t, const RunParams& p, int32_t i,
                                               uint32_t tau) {
-  return p.mtab ? __ldg(p.mtab + (int64_t)(tau - 1) * t.n + i) : __ldg(t.servers + i);
+  if (EXT && p.mtab) return __ldg(p.mtab + (int64_t)(tau - 1) * t.n + i);
+  return __ldg(t.servers + i);
 }
 
 __device__ __forceinline__ int64_t gather_in(const NetTables& t, int32_t i, const int32_t* redge,
@@ -88,21 +90,22 @@ struct UnitOut {
 // service stream.  One binomial call site serves the departure and every
 // routing edge, so lanes that took different branches of Algorithm 1 execute
 // the binomial together.
-template <bool GRAD>
+// EXT: the run may use a staffing schedule or the Eq. (1)/(2) samplers.
+template <bool GRAD, bool EXT>
 __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunParams& p, int32_t i,
                                                 uint32_t tau, uint32_t rep, int32_t y,
                                                 int32_t* redge, int64_t stride, int64_t col,
                                                 SamplerCtx& cx, int32_t& D, int32_t& X, float& smu) {
   PhiloxStream svc;
   svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
-  const int32_t m = servers_at(t, p, i, tau);
+  const int32_t m = servers_at<EXT>(t, p, i, tau);
   const int32_t e0 = __ldg(t.row_ptr + i);
   const int32_t deg = __ldg(t.row_ptr + i + 1) - e0;
   int32_t rem = 0;
   int32_t j0 = -1;
   D = 0;
   BinomialArgs dep;
-  if (p.dep_mode == 1 || (p.dep_mode == 2 && y > m)) {
+  if (EXT && (p.dep_mode == 1 || (p.dep_mode == 2 && y > m))) {
     // Eq. (1) (Eq. (2) for x > m): D = min(x, Poisson(min(x, m) mu h))
     const int32_t b = y < m ? y : m;
     const int32_t S = poisson((float)b * __ldg(p.muh + i), svc, cx);
@@ -145,7 +148,7 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
 //   FULL = true  (forward, Algorithm 3): x = N_{tau-1} + A^ex + A^in, N_tau = x - D.
 //   FULL = false (backward, Algorithm 2, first phase): x = N_{tau-1};
 //                stores N_{tau-1} - D + A^ex, the gather adds A^in later.
-template <bool FULL, bool GRAD = false>
+template <bool FULL, bool GRAD = false, bool EXT = true>
 __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunParams& p, int32_t i,
                                                uint32_t tau, uint32_t rep, const float* lam_t,
                                                int32_t* nstate, int32_t* redge, int64_t stride,
@@ -171,7 +174,7 @@ __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunPara
       x = kStateLimit;
     }
   }
-  serve_and_route<GRAD>(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X, o.smu);
+  serve_and_route<GRAD, EXT>(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X, o.smu);
   if (FULL) {
     o.N = (int32_t)x - o.D;
     nstate[(int64_t)i * stride + col] = o.N;

@@ -30,8 +30,8 @@ MUTANTS = [
     ("route_unconditional", "double q = suffix > 0.0 ? net->prob[e] / suffix : 0.0;",
      "double q = net->prob[e];"),
     # backward scheme: departures drawn after adding the step's arrivals
-    ("backward_order", "D[i] = departure(N[i], net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);",
-     "D[i] = departure(N[i] + (int32_t)(lam_t[i] > 0.0f ? 1 : 0), net->servers[i], mu_f[i], h_f, p0[i], &svc, &err, &smu);"),
+    ("backward_order", "D[i] = departure(N[i], m_t[i], mu_f[i], h_f, p0[i], muh[i], &svc, &err, &smu);",
+     "D[i] = departure(N[i] + (int32_t)(lam_t[i] > 0.0f ? 1 : 0), m_t[i], mu_f[i], h_f, p0[i], muh[i], &svc, &err, &smu);"),
     # likelihood-ratio score of the x <= m binomial: dp0/dmu factor dropped
     ("score_binomial", "if (score_mu) *score_mu = h * ((k > 0 ? (float)k / p0 : 0.0f) - (float)x);",
      "if (score_mu) *score_mu = ((k > 0 ? (float)k / p0 : 0.0f) - (float)x);"),
@@ -53,7 +53,7 @@ MUTANTS = [
     ("btrs_mode", "if (lv <= logpmf_binom(k, n, p, q) - lpm) return k;",
      "if (lv <= logpmf_binom(k, n, p, q)) return k;"),
     # statistics: busy servers counted as customers
-    ("stat_busy", "ss[1] += N[i] < net->servers[i] ? N[i] : net->servers[i];", "ss[1] += N[i];"),
+    ("stat_busy", "ss[1] += N[i] < m_t[i] ? N[i] : m_t[i];", "ss[1] += N[i];"),
     # Philox: a Weyl key constant slip
     ("philox_weyl", "#define PHILOX_W1 0xBB67AE85u", "#define PHILOX_W1 0xBB67AE84u"),
     # exp: a Taylor coefficient slip
