@@ -588,6 +588,15 @@ static void interval_rate_grad(const eo_net* net, int32_t i, int64_t tau, double
   g[2] = net->w[i] * net->a * net->b * ((s1 - s0) / om);
 }
 
+/* Servers of every station during step tau (Sec. 2.1.2): the staffing
+ * schedule at the step's start time (tau - 1) dt, or the constant m_i. */
+static const int32_t* servers_of_step(const eo_net* net, int64_t tau, double dt) {
+  if (!net->sv_table) return net->servers;
+  int64_t j = (int64_t)floor((double)(tau - 1) * dt / net->sv_dt);
+  if (j > net->sv_len - 1) j = net->sv_len - 1;
+  return net->sv_table + j * net->n;
+}
+
 int64_t eo_num_steps(double dt, double T) {
   double k = ceil(T / dt - 1e-9);
   return k < 1.0 ? 1 : (int64_t)k;
@@ -662,7 +671,7 @@ static int validate(const eo_net* net) {
  * those stations in index order. */
 static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T, int64_t R,
                          uint64_t seed, int64_t rep_begin, int64_t* stats, int32_t* trace_N,
-                         int32_t* trace_D, int32_t* trace_A, double* scores) {
+                         int32_t* trace_D, int32_t* trace_A, int32_t* trace_R, double* scores) {
   int rc = validate(net);
   if (rc) return rc;
   if (!(dt > 0.0) || !(T > 0.0) || R < 0 || rep_begin < 0 || !stats) return EO_ERR_ARG;
@@ -747,13 +756,7 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
       }
     for (int64_t tau = 1; tau <= K && !err; ++tau) {
       const float* lam_t = lam + (tau - 1) * n;
-      /* servers of this step: the schedule at the step's start time */
-      const int32_t* m_t = net->servers;
-      if (net->sv_table) {
-        int64_t j = (int64_t)floor((double)(tau - 1) * dt / net->sv_dt);
-        if (j > net->sv_len - 1) j = net->sv_len - 1;
-        m_t = net->sv_table + j * n;
-      }
+      const int32_t* m_t = servers_of_step(net, tau, dt);
       if (scheme == EO_BACKWARD) {
         /* Sec. 2.2 backward tasks 1-3 for every node from N_{tau-1} ... */
         for (int32_t i = 0; i < n; ++i) {
@@ -817,6 +820,8 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
           if (trace_A) trace_A[idx] = A[i];
         }
       }
+      if (trace_R)
+        for (int32_t e = 0; e < E; ++e) trace_R[((tau - 1) * E + e) * R + r] = Redge[e];
     }
     for (int32_t i = 0; i < n; ++i) st_NK[i] += N[i];
     if (scores) {
@@ -933,7 +938,7 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
                 int64_t rep_begin, int64_t* stats, int32_t* trace_N, int32_t* trace_D,
                 int32_t* trace_A) {
   return simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, trace_N, trace_D, trace_A,
-                       NULL);
+                       NULL, NULL);
 }
 
 /* Likelihood-ratio (score-function) gradient of the two measures
@@ -951,7 +956,7 @@ int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, u
   const int64_t C = n + 3;
   int64_t* stats = (int64_t*)malloc((size_t)(6 * (int64_t)n + 4 * R) * sizeof(int64_t));
   double* sc = scores_out ? scores_out : (double*)malloc((size_t)(R * C) * sizeof(double));
-  int rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, NULL, NULL, NULL, sc);
+  int rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, NULL, NULL, NULL, NULL, sc);
   if (rc == EO_OK) {
     const int64_t* rp = stats + 5 * (int64_t)n;
     for (int m = 0; m < 2; ++m) {
@@ -985,5 +990,147 @@ int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, u
   }
   if (!scores_out) free(sc);
   free(stats);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sojourn time of a tagged customer: Sec. 6, Algorithm 4, with the          */
+/* conditional probability of Lemma 3.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* b^k for an integer k >= 0 by binary powering (the multiplications in a
+ * fixed order, so both sides of the parity check round identically). */
+static float pow_int(float b, int32_t k) {
+  float r = 1.0f;
+  while (k > 0) {
+    if (k & 1) r = r * b;
+    b = b * b;
+    k >>= 1;
+  }
+  return r;
+}
+
+/* Lemma 3: a server busy with the tagged customer at the start of a step is
+ * still busy with it at the end, given that the step's departure draw had
+ * input x (customers at the station) and output d (m servers):
+ *   x <= m          : (x - d) / x
+ *   m < x <= m + d  : ((m-1)/m)^(x-m) (x - d) / m
+ *   x > m + d       : ((m-1)/m)^d
+ * d = 0 gives 1 in every case (also for an x = 0 that a sample path can show
+ * at the tagged customer's station: nothing left, so nothing ends service). */
+float eo_sojourn_pstay(int32_t x, int32_t d, int32_t m) {
+  if (d <= 0) return 1.0f;
+  if (x <= m) return (float)(x - d) / (float)x;
+  float q = (float)(m - 1) / (float)m;
+  if (x <= m + d) return pow_int(q, x - m) * ((float)(x - d) / (float)m);
+  return pow_int(q, d);
+}
+
+/* Algorithm 4 over stored sample paths.  The paths are simulated first with
+ * the given scheme (N_tau, D_tau and the routed counts R_tau,e of every step
+ * are kept); then, for every replication r and tagged customer s, the
+ * algorithm runs on path r:
+ *   Setup    at station i after step tau: position p = max(N_tau,i, 1); if
+ *            p > m_i wait, else serve.
+ *   Waiting  eta = min{j >= 1 : p - D_tau+1,i - ... - D_tau+j,i <= m_i};
+ *            T += eta h, tau += eta; then serve.
+ *   Service  step tau+1: stay with probability Lemma 3 (x, d) where d =
+ *            D_tau+1,i and x is the input of that departure draw (N_tau,i for
+ *            the backward scheme, N_tau+1,i + D_tau+1,i for the forward one);
+ *            T += h, tau += 1; on leaving, go to station j with probability
+ *            R_tau,ij / D_tau,i or exit with the remaining mass.
+ * m_i is the staffing of the step whose values are read.  Random choices use
+ * the stream (seed, purpose 3, station slot s, step tau, replication): its
+ * first uniform decides the stay (stay iff u < p_stay), its second word w
+ * picks the departing customer k = floor(w d / 2^32) among the d departures,
+ * which go, in CSR order, to the edges' destinations and then to the exit.
+ * out[r * samples + s] = the sojourn in steps (T / h) if the customer left
+ * by step K, else -(steps accounted up to step K) (censored; <= 0). */
+int eo_sojourn(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+               int64_t rep_begin, int32_t station, int64_t tau0, int32_t samples, int32_t* out,
+               int64_t* stats) {
+  int rc = validate(net);
+  if (rc) return rc;
+  const int32_t n = net->n;
+  const int32_t E = net->row_ptr[n];
+  const int64_t K = eo_num_steps(dt, T);
+  if (!(dt > 0.0) || !(T > 0.0) || R < 0 || samples < 1 || !out) return EO_ERR_ARG;
+  if (station < 0 || station >= n || tau0 < 1 || tau0 > K) return EO_ERR_ARG;
+  const size_t cells = (size_t)K * (size_t)n * (size_t)(R > 0 ? R : 1);
+  int32_t* tN = (int32_t*)malloc(cells * sizeof(int32_t));
+  int32_t* tD = (int32_t*)malloc(cells * sizeof(int32_t));
+  int32_t* tR = (int32_t*)malloc((size_t)K * (size_t)(E > 0 ? E : 1) * (size_t)(R > 0 ? R : 1) * sizeof(int32_t));
+  int64_t* st = stats ? stats : (int64_t*)malloc((size_t)(6 * (int64_t)n + 4 * R) * sizeof(int64_t));
+  if (!tN || !tD || !tR || !st) {
+    free(tN); free(tD); free(tR); if (!stats) free(st);
+    return EO_ERR_ARG;
+  }
+  rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, st, tN, tD, NULL, tR, NULL);
+  /* path values: step tau in 1..K, station i, replication r */
+#define PN(tau, i) tN[(((tau) - 1) * n + (i)) * R + r]
+#define PD(tau, i) tD[(((tau) - 1) * n + (i)) * R + r]
+#define PR(tau, e) tR[(((tau) - 1) * E + (e)) * R + r]
+  for (int64_t r = 0; r < R && rc == EO_OK; ++r) {
+    const uint32_t rep = (uint32_t)(rep_begin + r);
+    for (int32_t s = 0; s < samples; ++s) {
+      int32_t i = station;
+      int64_t tau = tau0;
+      int64_t steps = 0;
+      int done = 0;
+      while (!done) {
+        /* Setup step */
+        int32_t pos = PN(tau, i);
+        if (pos < 1) pos = 1;
+        if (pos > servers_of_step(net, tau, dt)[i]) {
+          /* Waiting step: eta steps until at most m_i are ahead of or at the
+             customer's place */
+          int64_t j = 0;
+          int64_t left = pos;
+          int reached = 0;
+          while (tau + j + 1 <= K) {
+            ++j;
+            left -= PD(tau + j, i);
+            if (left <= servers_of_step(net, tau + j, dt)[i]) { reached = 1; break; }
+          }
+          steps += j;
+          tau += j;
+          if (!reached) break; /* censored while waiting */
+        }
+        /* Service step, repeated while the customer stays */
+        for (;;) {
+          if (tau + 1 > K) { done = -1; break; } /* censored in service */
+          const int64_t t1 = tau + 1;
+          const int32_t d = PD(t1, i);
+          const int32_t x = scheme == EO_BACKWARD ? PN(tau, i) : PN(t1, i) + d;
+          const float ps = eo_sojourn_pstay(x, d, servers_of_step(net, t1, dt)[i]);
+          stream_t cs;
+          stream_init(&cs, seed, 3u, (uint32_t)s, (uint32_t)t1, rep);
+          const float u = next_uniform(&cs);
+          const uint32_t w = next_word(&cs);
+          steps += 1;
+          tau = t1;
+          if (u < ps) continue; /* I = 1: still in service */
+          /* I = 0: the customer is one of the d departures; its destination
+             follows the step's routed counts */
+          uint32_t k = (uint32_t)(((uint64_t)w * (uint64_t)(uint32_t)d) >> 32);
+          int32_t next = -1;
+          for (int32_t e = net->row_ptr[i]; e < net->row_ptr[i + 1]; ++e) {
+            const uint32_t v = (uint32_t)PR(t1, e);
+            if (k < v) { next = net->col[e]; break; }
+            k -= v;
+          }
+          if (next < 0) { done = 1; break; } /* exit: sojourn complete */
+          i = next;
+          break; /* back to the Setup step at the new station */
+        }
+      }
+      out[r * samples + s] = done == 1 ? (int32_t)steps : -(int32_t)steps;
+    }
+  }
+#undef PN
+#undef PD
+#undef PR
+  free(tN); free(tD); free(tR);
+  if (!stats) free(st);
   return rc;
 }

@@ -17,6 +17,7 @@
  *   - backward scheme: Sec. 2.2 task list 1-4 and Algorithm 2
  *   - forward scheme: Sec. 2.2 task list 1-4 and Algorithm 3 (node-by-node in
  *     flow order for a feedforward network)
+ *   - sojourn times: Sec. 6, Algorithm 4 and Lemma 3
  *
  * The paper does not specify the random-variate generators; the sampler
  * definitions below (Philox4x32-10 keying, uniform mapping, inversion /
@@ -88,6 +89,19 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T,
  * grad, grad_var: [2][n+3]; value: [2]; scores_out: [R][n+3] or NULL. */
 int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
             int64_t rep_begin, double* scores_out, double* grad, double* value, double* grad_var);
+
+/* Sojourn time of tagged customers (Sec. 6, Algorithm 4): a customer that
+ * enters `station` during step tau0 (1 <= tau0 <= K), `samples` tagged
+ * customers per replication, on the sample paths of eo_simulate with the same
+ * arguments.  out: [R][samples] int32, the sojourn in steps if the customer
+ * left by step K, else minus the steps accounted (censored, <= 0).  stats
+ * (optional, 6n + 4R) receives the paths' statistics.  See euler_oracle.c. */
+int eo_sojourn(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+               int64_t rep_begin, int32_t station, int64_t tau0, int32_t samples, int32_t* out,
+               int64_t* stats);
+/* Lemma 3: P(the tagged customer's service continues through a step | the
+ * step's departure draw had input x and output d, m servers). */
+float eo_sojourn_pstay(int32_t x, int32_t d, int32_t m);
 
 /* Number of Euler steps for a horizon: K = ceil(T/dt - 1e-9). */
 int64_t eo_num_steps(double dt, double T);

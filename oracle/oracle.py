@@ -19,7 +19,7 @@ __all__ = [
     "build_oracle", "lib", "simulate", "num_steps", "stats_split", "philox", "map_f32",
     "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
     "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
-    "BACKWARD", "FORWARD", "grad", "set_departure_mode",
+    "BACKWARD", "FORWARD", "grad", "set_departure_mode", "sojourn", "sojourn_pstay",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -93,6 +93,11 @@ def lib():
         L.eo_set_departure_mode.restype = C.c_int32
         L.eo_set_departure_mode.argtypes = [C.c_int32]
         L.eo_grad.restype = C.c_int
+        L.eo_sojourn.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
+                                 C.c_uint64, C.c_int64, C.c_int32, C.c_int64, C.c_int32,
+                                 C.c_void_p, C.c_void_p]
+        L.eo_sojourn_pstay.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+        L.eo_sojourn_pstay.restype = C.c_float
         L.eo_grad.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
                               C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = L
@@ -190,6 +195,30 @@ def grad(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, rep_
     if scores:
         out["scores"] = sc
     return out
+
+
+def sojourn(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, station: int,
+            tau0: int, samples: int = 1, rep_begin: int = 0, expect_ok: bool = True):
+    """Algorithm 4 on the oracle's sample paths (see eo_sojourn): dict with
+    'steps' [R, samples] int32 (> 0 completed, <= 0 censored) and the paths'
+    'stats' with their split views."""
+    L = lib()
+    s, keep = _make_net(net)
+    out = np.zeros((R, samples), dtype=np.int32)
+    stats = np.zeros(6 * net.n + 4 * R, dtype=np.int64)
+    rc = L.eo_sojourn(C.byref(s), scheme, dt, T, R, seed, rep_begin, station, tau0, samples,
+                      _ptr(out), _ptr(stats))
+    del keep
+    if expect_ok and rc != 0:
+        raise RuntimeError(f"oracle eo_sojourn failed with code {rc}")
+    res = {"rc": rc, "steps": out, "stats": stats}
+    res.update(stats_split(stats, net.n, R))
+    return res
+
+
+def sojourn_pstay(x: int, d: int, m: int) -> float:
+    """Lemma 3's stay probability as the oracle evaluates it (float32)."""
+    return float(lib().eo_sojourn_pstay(int(x), int(d), int(m)))
 
 
 def set_departure_mode(mode: int) -> int:

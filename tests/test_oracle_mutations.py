@@ -56,6 +56,18 @@ MUTANTS = [
     ("stat_busy", "ss[1] += N[i] < m_t[i] ? N[i] : m_t[i];", "ss[1] += N[i];"),
     # Philox: a Weyl key constant slip
     ("philox_weyl", "#define PHILOX_W1 0xBB67AE85u", "#define PHILOX_W1 0xBB67AE84u"),
+    # Lemma 3, m < x <= m + d: exponent x - m written as d
+    ("sojourn_lemma3_exponent", "if (x <= m + d) return pow_int(q, x - m) * ((float)(x - d) / (float)m);",
+     "if (x <= m + d) return pow_int(q, d) * ((float)(x - d) / (float)m);"),
+    # Algorithm 4, backward scheme: post-update count taken as the draw's input
+    ("sojourn_backward_x", "const int32_t x = scheme == EO_BACKWARD ? PN(tau, i) : PN(t1, i) + d;",
+     "const int32_t x = scheme == EO_BACKWARD ? PN(t1, i) : PN(t1, i) + d;"),
+    # Algorithm 4 waiting step: <= m_i written as < m_i
+    ("sojourn_wait_threshold", "if (left <= servers_of_step(net, tau + j, dt)[i]) { reached = 1; break; }",
+     "if (left < servers_of_step(net, tau + j, dt)[i]) { reached = 1; break; }"),
+    # Algorithm 4 routing: departing customer picked with an off-by-one
+    ("sojourn_route_pick", "if (k < v) { next = net->col[e]; break; }",
+     "if (k <= v) { next = net->col[e]; break; }"),
     # exp: a Taylor coefficient slip
     ("exp_coeff", "p = fmaf(p, r, (float)(1.0 / 6.0));", "p = fmaf(p, r, (float)(1.0 / 7.0));"),
 ]

@@ -16,7 +16,10 @@ a transposed routing index, a wrong arrival integral -- fails at least one:
 * the exact single-station distribution by brute-force convolution;
 * Argument 2 and Argument 3 (Sec. 4.1), Theorem 1's steady-state bracketing
   of the Erlang-C mean and gap lambda*h, Theorem 2's per-node gap;
-* the arrival integral of Sec. 2.1.1 and the bookkeeping invariants.
+* the arrival integral of Sec. 2.1.1 and the bookkeeping invariants;
+* the sojourn sampler of Sec. 6 (Algorithm 4): Lemma 3 against the exact
+  tagged-server chain by brute force, and the sojourn law in cases where it is
+  known exactly (infinite servers, pure-departure waiting, routing mixture).
 """
 import math
 import os
@@ -661,3 +664,162 @@ def test_staffing_schedule_exact_distribution(orc, scheme):
     base = orc.simulate(net2, scheme, h, K * h, 500, 43)["stats"]
     net2.servers_schedule, net2.servers_schedule_dt = np.array([[4]], dtype=np.int32), 1.0
     assert np.array_equal(orc.simulate(net2, scheme, h, K * h, 500, 43)["stats"], base)
+
+
+# ---------------------------------------------------------------------------
+# Sojourn time (Sec. 6, Algorithm 4, Lemma 3)
+# ---------------------------------------------------------------------------
+def _lemma3_exact(x, m, mu, h):
+    """P(tagged server still busy with the same customer | D = d), d = 0..x,
+    from the pure departure process with a tagged server: states (y, e), y
+    customers left, e = 1 while the tagged customer is still in service."""
+    S = 2 * (x + 1)
+    Q = np.zeros((S, S))
+    for y in range(1, x + 1):
+        busy = min(y, m)
+        # tagged still in service: its own completion, or one of the others
+        Q[2 * y + 1, 2 * (y - 1) + 0] += mu
+        Q[2 * y + 1, 2 * (y - 1) + 1] += (busy - 1) * mu
+        # tagged gone: every busy server completes at rate mu
+        Q[2 * y + 0, 2 * (y - 1) + 0] += busy * mu
+    for k in range(S):
+        Q[k, k] = -Q[k].sum()
+    P = expm(Q * h)[2 * x + 1]
+    out = {}
+    for d in range(x + 1):
+        y = x - d
+        tot = P[2 * y] + P[2 * y + 1]
+        if tot > 1e-13:
+            out[d] = P[2 * y + 1] / tot
+    return out
+
+
+@pytest.mark.parametrize("x,m", [(1, 1), (4, 6), (6, 6), (7, 6), (9, 3), (15, 4), (12, 1), (30, 8)])
+@pytest.mark.parametrize("muh", [0.3, 2.0])
+def test_sojourn_lemma3_exact(orc, x, m, muh):
+    """Lemma 3: the stay probability given the step's departures equals the
+    tagged-server chain's conditional probability (and does not depend on mu h)."""
+    ex = _lemma3_exact(x, m, 1.0, muh)
+    for d, want in ex.items():
+        got = orc.sojourn_pstay(x, d, m)
+        assert abs(got - want) <= 2e-6 * max(want, 1e-3), (x, m, d, got, want)
+
+
+def _geom_pmf(p, kmax):
+    k = np.arange(1, kmax + 1)
+    return (1.0 - p) ** (k - 1) * p
+
+
+def _p0(mu, h):
+    return float(-np.expm1(-np.float64(np.float32(mu * h))))
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_sojourn_infinite_server_geometric(orc, scheme):
+    """With more servers than customers a customer in service stays through a
+    step with probability E[(x - D)/x] = e^{-mu h} for D ~ Bin(x, p0): the
+    sojourn in steps is Geometric(p0) exactly, censored at the horizon."""
+    mu, h, lam, N0, K, tau0, R = 1.0, 0.05, 400.0, 400, 200, 20, 20000
+    run = W.single_station(1_000_000, mu, lam, h, K * h, R, 61, N0=N0)
+    res = orc.sojourn(run.net, scheme, h, K * h, R, run.seed, station=0, tau0=tau0)
+    s = res["steps"][:, 0]
+    kmax = K - tau0
+    pmf = _geom_pmf(_p0(mu, h), kmax)
+    obs = np.concatenate([np.bincount(s[s > 0], minlength=kmax + 1)[1:], [(s <= 0).sum()]])
+    exp_ = np.concatenate([pmf, [1.0 - pmf.sum()]]) * R
+    assert s.min() >= -kmax and s.max() <= kmax
+    assert _chi2_p(obs, exp_) > 1e-4
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_sojourn_waiting_pure_departure(orc, scheme):
+    """No arrivals, m servers, the tagged customer last of the p = N_tau0 at
+    the station: it reaches a server in the step of the (p - m)-th departure,
+    a Gamma(p - m, m mu) time after tau0 h (the paths are exact pure-departure
+    paths, Lemma 1), then serves a Geometric(p0) number of steps: S =
+    ceil(Gamma / h) + Geometric(p0); S = Geometric(p0) when p <= m."""
+    m, mu, h, N0, K, tau0, R = 3, 1.0, 0.02, 12, 1000, 1, 10000
+    run = W.single_station(m, mu, 0.0, h, K * h, R, 62, N0=N0)
+    res = orc.sojourn(run.net, scheme, h, K * h, R, run.seed, station=0, tau0=tau0)
+    s = res["steps"][:, 0]
+    # N_tau0 of every path: the first step only (same keys)
+    pos = orc.simulate(run.net, scheme, h, tau0 * h, R, run.seed, trace=True)["N"][tau0 - 1, 0]
+    hf = float(np.float32(h))
+    kmax = K - tau0
+    geo = _geom_pmf(_p0(mu, h), kmax)
+    mix = np.zeros(kmax)
+    for p, cnt in zip(*np.unique(pos, return_counts=True)):
+        p = max(int(p), 1)
+        if p <= m:
+            law = geo
+        else:
+            F = stats.gamma.cdf(np.arange(0, kmax + 1) * hf, p - m, scale=1.0 / (m * mu))
+            eta = np.diff(F)  # P(eta = j), j = 1..kmax
+            law = np.convolve(eta, geo)[: kmax]
+            law = np.concatenate([[0.0], law[:-1]])  # eta >= 1 then >= 1 service step
+        mix += cnt * law
+    obs = np.concatenate([np.bincount(s[s > 0], minlength=kmax + 1)[1:], [(s <= 0).sum()]])
+    exp_ = np.concatenate([mix, [R - mix.sum()]])
+    assert (pos > m).mean() > 0.5  # the waiting step is exercised
+    assert _chi2_p(obs, exp_) > 1e-4
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_sojourn_heavy_load_service_is_geometric(orc, scheme):
+    """A customer that finds a free server (N_tau0 <= m) stays through each
+    later step with probability e^{-mu h} whatever the queue behind it: Lemma
+    3's x > m branches averaged over the step's departure law.  The load keeps
+    x > m in many of those steps."""
+    m, mu, lam, h, K, tau0, R = 3, 1.0, 4.5, 0.05, 330, 30, 40000
+    run = W.single_station(m, mu, lam, h, K * h, R, 63)
+    res = orc.sojourn(run.net, scheme, h, K * h, R, run.seed, station=0, tau0=tau0)
+    tr = orc.simulate(run.net, scheme, h, (tau0 + 20) * h, R, run.seed, trace=True)["N"][:, 0]
+    sel = tr[tau0 - 1] <= m
+    assert sel.mean() > 0.3
+    assert (tr[tau0 + 15][sel] > m).mean() > 0.4  # queues behind the customer
+    s = res["steps"][sel, 0]
+    kmax = K - tau0
+    pmf = _geom_pmf(_p0(mu, h), kmax)
+    obs = np.concatenate([np.bincount(s[s > 0], minlength=kmax + 1)[1:], [(s <= 0).sum()]])
+    exp_ = np.concatenate([pmf, [1.0 - pmf.sum()]]) * sel.sum()
+    assert _chi2_p(obs, exp_) > 1e-4
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_sojourn_routing_mixture(orc, scheme):
+    """Two infinite-server stations, 0 -> 1 with probability p, else exit: the
+    customer leaves station 0 to station 1 with probability E[R/D] = p, so S =
+    G0 + B G1 with G_i ~ Geometric(p0_i), B ~ Bernoulli(p), independent."""
+    p, mu0, mu1, h, K, tau0, R = 0.6, 1.0, 0.25, 0.05, 700, 20, 20000
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, p)])
+    arr = W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([40.0, 0.0]), a=1.0, b=0.0)
+    net = W.Network(2, row_ptr, col, prob, np.full(2, 1_000_000), np.array([mu0, mu1]), arr,
+                    N0=np.array([40, 96], dtype=np.int32))
+    res = orc.sojourn(net, scheme, h, K * h, R, 64, station=0, tau0=tau0)
+    s = res["steps"][:, 0]
+    kmax = K - tau0
+    g0 = _geom_pmf(_p0(mu0, h), kmax)
+    g1 = _geom_pmf(_p0(mu1, h), kmax)
+    both = np.concatenate([[0.0], np.convolve(g0, g1)[: kmax - 1]])
+    mix = (1.0 - p) * g0 + p * both
+    obs = np.concatenate([np.bincount(s[s > 0], minlength=kmax + 1)[1:], [(s <= 0).sum()]])
+    exp_ = np.concatenate([mix, [1.0 - mix.sum()]]) * R
+    assert _chi2_p(obs, exp_) > 1e-4
+
+
+def test_sojourn_bookkeeping(orc):
+    """Censoring at the horizon, replication keying, the paths' statistics and
+    argument errors."""
+    run = W.tandem3(R=64)
+    net, dt = run.net, run.dt
+    K = orc.num_steps(dt, 2.0)
+    full = orc.sojourn(net, 0, dt, 2.0, 64, 5, station=0, tau0=50, samples=3)
+    assert np.array_equal(full["stats"], orc.simulate(net, 0, dt, 2.0, 64, 5)["stats"])
+    sub = orc.sojourn(net, 0, dt, 2.0, 20, 5, station=0, tau0=50, samples=3, rep_begin=30)
+    assert np.array_equal(sub["steps"], full["steps"][30:50])
+    last = orc.sojourn(net, 1, dt, 2.0, 64, 5, station=1, tau0=K, samples=2)
+    assert (last["steps"] == 0).all()  # entered in the last step: censored, nothing accounted
+    st = full["steps"]
+    assert st.max() <= K - 50 and st.min() >= -(K - 50)
+    for bad in (dict(station=3, tau0=1), dict(station=0, tau0=0), dict(station=0, tau0=K + 1)):
+        assert orc.sojourn(net, 0, dt, 2.0, 4, 5, expect_ok=False, **bad)["rc"] != 0
