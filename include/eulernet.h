@@ -196,6 +196,33 @@ EULERNET_API int euler_net_grad(euler_net* net, int32_t scheme, double dt, doubl
                                 double* grad, double* value, double* grad_var, double* scores,
                                 int64_t* stats, void* cuda_stream);
 
+/* ---- Sojourn times (Sec. 6, Algorithm 4) ---- */
+
+/* Sojourn times of tagged customers that enter `station` during step tau0
+ * (the interval ((tau0-1) dt, tau0 dt], 1 <= tau0 <= K), `samples` tagged
+ * customers per replication, sampled on the replications' own Euler sample
+ * paths (those euler_net_simulate produces with the same arguments) by
+ * Algorithm 4: a customer waits at a station while more than m_i customers
+ * are ahead of or at its place (its place is N_tau,i after the step it
+ * arrived in), and in service it stays through a step with the probability
+ * of Lemma 3 given that step's departure draw (input x, output D); leaving,
+ * it follows the step's routed counts R_e / D or exits.  Each step counts h.
+ *   sojourn  DEVICE [R][samples] int32 out: the sojourn in steps (> 0) if the
+ *            customer left by step K, else minus the steps accounted (<= 0,
+ *            censored at the horizon)
+ *   stats    DEVICE stats buffer of the sample paths (as euler_net_simulate),
+ *            or NULL
+ * The random choices use the Philox stream (seed, purpose 3, sample index,
+ * step, rep_begin + r): the first uniform decides the stay, the second word
+ * picks the departing customer.  Results do not depend on the launch.
+ * Asynchronous on cuda_stream.  EULER_ERR_ARG for a station or tau0 out of
+ * range or samples outside [1, 65536]; EULER_ERR_TOO_LARGE when a tile with
+ * its customers does not fit in shared memory. */
+EULERNET_API int euler_net_sojourn(euler_net* net, int32_t scheme, double dt, double T,
+                                   int64_t replications, uint64_t seed, int64_t rep_begin,
+                                   int32_t station, int64_t tau0, int32_t samples, int32_t* sojourn,
+                                   int64_t* stats, void* cuda_stream);
+
 /* ---- Batched form: many independent networks in one persistent launch ---- */
 
 /* One simulation request of a batch (see euler_net_simulate for the fields). */

@@ -90,6 +90,8 @@ def lib():
         L.euler_net_batch_simulate.restype = C.c_int
         L.euler_net_grad.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp, vp, vp, vp, vp]
         L.euler_net_grad.restype = C.c_int
+        L.euler_net_sojourn.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, i32, i64, i32, vp, vp, vp]
+        L.euler_net_sojourn.restype = C.c_int
         L.euler_net_simulate_average.argtypes = [vp, dbl, dbl, i64, u64, i64, vp, vp, vp, vp]
         L.euler_net_simulate_average.restype = C.c_int
         L.euler_net_select_dt.argtypes = [vp, dbl]
@@ -254,6 +256,22 @@ class EulerNet:
         _check(lib().euler_net_grad(self._h, scheme, dt, T, R, seed, rep_begin, ptr("grad"), ptr("value"),
                                     ptr("var"), ptr("scores"), ptr("stats"),
                                     C.c_void_p(_stream_ptr(stream))))
+        if check:
+            self.status(stream)
+        return out
+
+    def sojourn(self, scheme: int, dt: float, T: float, R: int, seed: int, station: int, tau0: int,
+                samples: int = 1, rep_begin: int = 0, out=None, stats=None, stream=None,
+                check: bool = True):
+        """Sojourn times of tagged customers entering `station` during step
+        tau0 (see euler_net_sojourn): int32 device tensor [R, samples], the
+        sojourn in steps (> 0) or minus the steps accounted when censored."""
+        import torch
+        if out is None:
+            out = torch.empty((R, samples), dtype=torch.int32, device="cuda")
+        sp = None if stats is None else C.c_void_p(stats.data_ptr())
+        _check(lib().euler_net_sojourn(self._h, scheme, dt, T, R, seed, rep_begin, station, tau0, samples,
+                                       C.c_void_p(out.data_ptr()), sp, C.c_void_p(_stream_ptr(stream))))
         if check:
             self.status(stream)
         return out

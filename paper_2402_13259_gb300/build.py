@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library ``libeulernet.so`` (sm_103a only).
 
-The two translation units are compiled in parallel with nvcc and linked
+The translation units are compiled in parallel with nvcc and linked
 against the shared CUDA runtime.  Float semantics: no multiply-add
 contraction, IEEE division and square root, denormals kept -- the samplers
 rely on every float operation being the correctly rounded one written in the
@@ -17,8 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeulernet.so")
-SOURCES = ["kernels.cu", "pipeline.cu", "abi.cu", "noalloc.cu", "batch.cu"]
-HEADERS = ["sampling.cuh", "internal.h", "handle.h", "unit.cuh", os.path.join("..", "..", "include", "eulernet.h")]
+SOURCES = ["kernels.cu", "pipeline.cu", "abi.cu", "noalloc.cu", "batch.cu", "sojourn.cu"]
+HEADERS = ["sampling.cuh", "internal.h", "handle.h", "unit.cuh", "tile.cuh", os.path.join("..", "..", "include", "eulernet.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -421,6 +421,8 @@ void euler_net_destroy(euler_net* h) {
   cudaFree(h->d_avg_f);
   cudaFree(h->d_mtab);
   cudaFree(h->d_muh);
+  cudaFree(h->d_col);
+  cudaFree(h->d_sstats);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }

@@ -58,6 +58,10 @@ struct euler_net {
   int64_t* d_avg_f = nullptr;
   size_t avg_cap = 0;
 
+  // sojourn-time sampler: edge destinations and a statistics scratch
+  int32_t* d_col = nullptr;
+  int64_t* d_sstats = nullptr;
+  size_t sstats_cap = 0;
   // HBM-form state
   int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr;
   int64_t* d_racc = nullptr;

@@ -23,221 +23,12 @@
 
 #include "internal.h"
 #include "sampling.cuh"
+#include "tile.cuh"
 #include "unit.cuh"
 
 namespace eulernet {
 
 namespace {
-
-// Per-station sums of a CTA into the stats buffer (integer atomics, so the
-// result does not depend on the order).
-__device__ __forceinline__ void flush_station_sums(const NetTables& t, const RunParams& p,
-                                                   const long long* sacc) {
-  const int32_t n = t.n;
-  int64_t* st_nk = p.stats + 5 * (int64_t)n + 4 * p.R;
-  for (int64_t k = threadIdx.x; k < 6 * (int64_t)n; k += blockDim.x) {
-    const int64_t i = k / 6, s = k % 6;
-    const long long v = sacc[k];
-    if (v == 0) continue;
-    unsigned long long* dst =
-        reinterpret_cast<unsigned long long*>(s < 5 ? p.stats + i * 5 + s : st_nk + i);
-    atomicAdd(dst, (unsigned long long)v);
-  }
-}
-
-// ---- persistent shared-memory form -------------------------------------------
-
-// Pointers into a CTA's working area for one tile of `Rt` replications of one
-// network.  sacc may live in shared memory or, for networks whose per-station
-// accumulators do not fit, in a global scratch slot owned by the CTA.
-struct TileSmem {
-  float* rinv;      // [64] 1/k
-  long long* sacc;  // [n][6] per-station sums (owned by this CTA)
-  long long* racc;  // [Rt][4] per-replication sums of the tile
-  int32_t* Ns;      // [n][Rt] state
-  int32_t* Rs;      // [E][Rt] routed counts
-  int* claim;       // [2] dynamic station claims per phase parity
-  double* mu_acc;   // GRAD: [n][Rt] score sums in mu_i
-  double* th_acc;   // GRAD: [n_ex][Rt][3] score sums in (a, b, phase) per external station
-};
-
-// Score terms of one unit into the tile's accumulators (GRAD kernels).
-__device__ __forceinline__ void add_scores(const NetTables& t, const RunParams& p, const TileSmem& sm,
-                                           int32_t i, int32_t tau, int r, int Rt, const UnitOut& o) {
-  sm.mu_acc[(int64_t)i * Rt + r] += (double)o.smu;
-  if (!isnan(o.garr)) {
-    const int32_t ec = __ldg(t.ex_col + i);
-    const float* dl = p.dlam + ((int64_t)(tau - 1) * t.n_ex + ec) * 3;
-    double* th = sm.th_acc + ((int64_t)ec * Rt + r) * 3;
-    th[0] += (double)(o.garr * __ldg(dl + 0));
-    th[1] += (double)(o.garr * __ldg(dl + 1));
-    th[2] += (double)(o.garr * __ldg(dl + 2));
-  }
-}
-
-// One tile: the whole time loop for replications tile*Rt ... of network t.
-// Adds per-station sums (and N_K) into sm.sacc and writes the tile's
-// per-replication sums to p.stats.  Ends with a block barrier.
-template <int SCHEME, bool GRAD = false, bool EXT = true>
-__device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p, int64_t tile,
-                                          const TileSmem& sm, SamplerCtx& cx) {
-  const int32_t n = t.n;
-  const int Rt = p.tile_reps;
-  long long* sacc = sm.sacc;
-  long long* racc = sm.racc;
-  int32_t* Ns = sm.Ns;
-  int32_t* Rs = sm.Rs;
-  int* claim = sm.claim;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int r = tid % Rt;
-  const int g0 = tid / Rt;
-  const int G = nthr / Rt;
-  const int lane = tid & 31;
-  const int w = Rt < 32 ? Rt : 32;
-  const int gwarp = (tid & ~31) / Rt;  // group of lane 0 of this warp
-  const bool lead = (lane & (w - 1)) == 0;
-  const bool shared_station = Rt > 32;  // several warps per station -> atomics
-  // With one warp per station-unit (Rt = 32) warps claim the stations of a
-  // phase dynamically; claim[phase parity] counts the stations handed out.
-  const bool dynamic = Rt == 32;
-  int phase = 0;
-
-    const int64_t rloc = tile * Rt + r;
-    const bool rvalid = rloc < p.R;
-    const uint32_t rep = (uint32_t)(p.rep_begin + rloc);
-    for (int64_t k = tid; k < (int64_t)n * Rt; k += nthr)
-      Ns[k] = t.N0 ? __ldg(t.N0 + k / Rt) : 0;
-    for (int k = tid; k < 4 * Rt; k += nthr) racc[k] = 0;
-    if (GRAD) {
-      for (int64_t k = tid; k < (int64_t)n * Rt; k += nthr) sm.mu_acc[k] = 0.0;
-      for (int64_t k = tid; k < 3 * (int64_t)t.n_ex * Rt; k += nthr) sm.th_acc[k] = 0.0;
-    }
-    if (tid < 2) claim[tid] = 0;
-    phase = 0;
-    long long q_r = 0, d_r = 0, x_r = 0, a_r = 0;
-    __syncthreads();
-
-    // next station slot of this warp in the current phase (m slots)
-    auto next_slot = [&](int su0, int m) -> int {
-      if (!dynamic) return su0 + G;
-      int s = 0;
-      if (lane == 0) s = atomicAdd(&claim[phase & 1], 1);
-      return __shfl_sync(kFull, s, 0);
-    };
-    auto first_slot = [&]() -> int {
-      if (!dynamic) return gwarp;
-      if (tid == 0) claim[(phase + 1) & 1] = 0;  // counter of the next phase
-      int s = 0;
-      if (lane == 0) s = atomicAdd(&claim[phase & 1], 1);
-      return __shfl_sync(kFull, s, 0);
-    };
-
-    for (int32_t tau = 1; tau <= p.K; ++tau) {
-      const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
-      if (SCHEME == 0) {
-        for (int su0 = first_slot(); su0 < n; su0 = next_slot(su0, n)) {
-          const int su = su0 + (g0 - gwarp);
-          const bool act = rvalid && su < n;
-          int32_t v[3] = {0, 0, 0};
-          if (act) {
-            const UnitOut o = unit_update<false, GRAD, EXT>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
-            if (GRAD) add_scores(t, p, sm, su, tau, r, Rt, o);
-            v[0] = o.D;
-            v[1] = o.X;
-            v[2] = o.A;
-            d_r += o.D;
-            x_r += o.X;
-            a_r += o.A;
-          }
-          reduce_to<3>(sacc + 6 * (int64_t)(su < n ? su : 0) + 2, v, lead && su < n, w,
-                       shared_station);
-        }
-        ++phase;
-        __syncthreads();
-        for (int su0 = first_slot(); su0 < n; su0 = next_slot(su0, n)) {
-          const int su = su0 + (g0 - gwarp);
-          const bool act = rvalid && su < n;
-          int32_t v[2] = {0, 0};
-          if (act) {
-            const int32_t nn = backward_gather(t, su, Ns, Rs, Rt, r, cx.err);
-            const int32_t c = servers_at<EXT>(t, p, su, (uint32_t)tau);
-            v[0] = nn;
-            v[1] = nn < c ? nn : c;
-            q_r += nn;
-          }
-          reduce_to<2>(sacc + 6 * (int64_t)(su < n ? su : 0), v, lead && su < n, w, shared_station);
-        }
-        ++phase;
-        __syncthreads();
-      } else {
-        for (int32_t j = 0; j < t.L; ++j) {
-          const int32_t s0 = __ldg(t.lvl_ptr + j);
-          const int32_t m = __ldg(t.lvl_ptr + j + 1) - s0;
-          for (int su0 = first_slot(); su0 < m; su0 = next_slot(su0, m)) {
-            const int su = su0 + (g0 - gwarp);
-            const bool act = rvalid && su < m;
-            const int32_t i = su < m ? __ldg(t.lvl_station + s0 + su) : 0;
-            int32_t v[5] = {0, 0, 0, 0, 0};
-            if (act) {
-              const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
-              if (GRAD) add_scores(t, p, sm, i, tau, r, Rt, o);
-              const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
-              v[0] = o.N;
-              v[1] = o.N < c ? o.N : c;
-              v[2] = o.D;
-              v[3] = o.X;
-              v[4] = o.A;
-              q_r += o.N;
-              d_r += o.D;
-              x_r += o.X;
-              a_r += o.A;
-            }
-            reduce_to<5>(sacc + 6 * (int64_t)i, v, lead && su < m, w, shared_station);
-          }
-          ++phase;
-          __syncthreads();
-        }
-      }
-    }
-
-    // tile epilogue: per-replication sums and N_K
-    if (rvalid) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 0), (unsigned long long)q_r);
-      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 1), (unsigned long long)d_r);
-      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 2), (unsigned long long)x_r);
-      atomicAdd(reinterpret_cast<unsigned long long*>(racc + 4 * r + 3), (unsigned long long)a_r);
-    }
-    for (int su0 = gwarp; su0 < n; su0 += G) {
-      const int su = su0 + (g0 - gwarp);
-      int32_t v[1] = {(rvalid && su < n) ? Ns[(int64_t)su * Rt + r] : 0};
-      reduce_to<1>(sacc + 6 * (int64_t)(su < n ? su : 0) + 5, v, lead && su < n, w, shared_station);
-    }
-    __syncthreads();
-    int64_t* st_rep = p.stats + 5 * (int64_t)n;
-    for (int k = tid; k < 4 * Rt; k += nthr) {
-      const int64_t rr = tile * Rt + k / 4;
-      if (rr < p.R) st_rep[rr * 4 + (k & 3)] = racc[k];
-    }
-    if (GRAD) {
-      // S_r: mu_i sums, then (a, b, phase) summed over external stations in order
-      const int64_t C = (int64_t)n + 3;
-      for (int64_t k = tid; k < C * Rt; k += nthr) {
-        const int rr = (int)(k % Rt);
-        const int64_t c = k / Rt;
-        const int64_t rg = tile * Rt + rr;
-        if (rg >= p.R) continue;
-        double v;
-        if (c < n) {
-          v = sm.mu_acc[c * Rt + rr];
-        } else {
-          v = 0.0;
-          for (int32_t ec = 0; ec < t.n_ex; ++ec) v += sm.th_acc[((int64_t)ec * Rt + rr) * 3 + (c - n)];
-        }
-        p.scores[rg * C + c] = v;
-      }
-    }
-    __syncthreads();
-}
 
 // Single network: CTAs loop over the tiles.
 template <int SCHEME, bool GRAD = false, bool EXT = true>
@@ -264,8 +55,9 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunPara
   for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sm.sacc[k] = 0;
   SamplerCtx cx{sm.rinv, p.cap, 0u};
   __syncthreads();
+  NoHook hook;
   for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
-    tile_body<SCHEME, GRAD, EXT>(t, p, tile, sm, cx);
+    tile_body<SCHEME, GRAD, EXT>(t, p, tile, sm, cx, hook);
   flush_station_sums(t, p, sm.sacc);
   latch(p.err, cx.err);
 }
@@ -378,7 +170,10 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
     sm.claim = claim;
     for (int64_t k = tid; k < 6 * (int64_t)n; k += nthr) sm.sacc[k] = 0;
     __syncthreads();
-    tile_body<SCHEME, false, EXT>(t, p, wi.y, sm, cx);
+    {
+      NoHook hook;
+      tile_body<SCHEME, false, EXT>(t, p, wi.y, sm, cx, hook);
+    }
     flush_station_sums(t, p, sm.sacc);
     __syncthreads();
     err |= cx.err;

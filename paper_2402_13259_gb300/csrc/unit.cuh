@@ -81,6 +81,7 @@ __device__ __forceinline__ void reduce_to(long long* dst, const int32_t (&v)[NV]
 
 struct UnitOut {
   int32_t N, D, X, A;
+  int32_t x;   // input count of the departure draw
   float smu;   // score term of the departure in mu_i (GRAD only)
   float garr;  // A/Lambda - 1 of an external-arrival draw, NaN if none (GRAD only)
 };
@@ -175,6 +176,7 @@ __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunPara
     }
   }
   serve_and_route<GRAD, EXT>(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X, o.smu);
+  o.x = (int32_t)x;
   if (FULL) {
     o.N = (int32_t)x - o.D;
     nstate[(int64_t)i * stride + col] = o.N;

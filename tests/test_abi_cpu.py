@@ -78,3 +78,12 @@ def test_valid_network_without_gpu_fails_loudly(L):
         pytest.skip("a GPU is present")
     rc, h = _create(L, 2, [(0, 1, 0.5)])
     assert rc == -3 and not h.value  # EULER_ERR_CUDA, no handle, no CPU fallback
+
+
+def test_null_handle_is_an_argument_error(L):
+    from paper_2402_13259_gb300 import binding as Bd
+    assert L.euler_net_simulate(None, 0, 0.01, 1.0, 10, 1, 0, None, None) == -1
+    assert L.euler_net_sojourn(None, 0, 0.01, 1.0, 10, 1, 0, 0, 1, 1, None, None, None) == -1
+    assert L.euler_net_grad(None, 0, 0.01, 1.0, 10, 1, 0, None, None, None, None, None, None) == -1
+    assert L.euler_net_simulate_average(None, 0.01, 1.0, 10, 1, 0, None, None, None, None) == -1
+    assert isinstance(Bd.lib().euler_net_last_error(), bytes)
