@@ -8,6 +8,9 @@ step = one backward-scheme run plus one forward-scheme run over the whole
 workload (2 x 10^10 station-step updates), through the library's C ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload batch512   (batched form vs one launch per network)
+    python bench.py --workload rows --steps 1   (average scheme, sojourn times,
+        staffing schedules, Eq. (1)/(2) departures, gradients, scale sweep)
 
 Under torchrun each rank runs its own replication range (replication
 indices rank*R ... rank*R+R-1: weak scaling, no data-path collective); rank 0
@@ -32,19 +35,52 @@ METRIC = "station-step updates/s per GB300 (fwd/bwd Euler), % of binding rooflin
 UNIT = "station-step updates/s"
 SMS = 152
 LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
-# DRAM bytes per launch of the persistent kernel from ncu (profiles/), valid for
-# the kernel sources with this hash; None when the sources changed since.
-# profiles/persistent_kernel_dag100.md: 372 KB and 220 KB per launch of 2.05e8
-# units (backward, forward), scaled to 1e10 units by the unit count.
-TRAFFIC = {"hash": "04c15bc95ae45b57", "bytes_per_launch": 0.5 * (372e3 + 220e3) * 1e10 / 2.048e8}
+# DRAM bytes of one simulate call (mean of the two schemes) from ncu counters
+# (profiles/), valid only for the kernel sources with this hash and the launch
+# forms listed; reported as null otherwise.
+TRAFFIC = {"hash": None, "forms": None, "bytes_per_call": None}
 
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "sampling.cuh"):
+    for f in ("kernels.cu", "tile.cuh", "unit.cuh", "sampling.cuh"):
         with open(os.path.join(ROOT, "paper_2402_13259_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def num_levels(net) -> int:
+    """Longest-path levels of the feedforward network (the forward scheme's
+    flow order)."""
+    level = [0] * net.n
+    indeg = [0] * net.n
+    for e in range(int(net.row_ptr[-1])):
+        indeg[int(net.col[e])] += 1
+    order = [i for i in range(net.n) if indeg[i] == 0]
+    k = 0
+    while k < len(order):
+        i = order[k]
+        k += 1
+        for e in range(int(net.row_ptr[i]), int(net.row_ptr[i + 1])):
+            j = int(net.col[e])
+            level[j] = max(level[j], level[i] + 1)
+            indeg[j] -= 1
+            if indeg[j] == 0:
+                order.append(j)
+    return max(level) + 1
+
+
+def launches_per_call(plan, scheme: int, K: int, L: int) -> int:
+    """Kernels one euler_net_simulate call launches: the persistent kernel,
+    or (HBM form) init + graph replays of 32 slots of one kernel each
+    (backward: K + 1 fused slots; forward: K + L - 1 skewed slots) and one
+    counter advance per replay + finish."""
+    if plan["form"] != 2:
+        return 1
+    slots = K + 1 if scheme == 0 else K + L - 1
+    S = min(slots, 32)
+    replays = -(-slots // S)
+    return 2 + replays * (S + 1)
 
 
 def workload(args=None):
@@ -232,6 +268,134 @@ def run_batch_comparison(args):
     return 0
 
 
+def run_rows(args):
+    """The method's other rows on the 100-station DAG at full size, each
+    through its C-ABI entry point and timed with CUDA events on the launching
+    stream (one warm-up call with the same dt and T first): the average
+    scheme, sojourn times, a staffing schedule, the Eq. (1)/(2) departure
+    samplers, likelihood-ratio gradients (100,000 replications of the
+    sinusoid-arrival DAG) and the staffing-scale sweep (2,000 stations,
+    dt = 1/sqrt(s), 2,048 replications).  One JSON line per row; bit-exact
+    parity of each row is in the GPU tests."""
+    import numpy as np
+    import torch
+    from paper_2402_13259_gb300 import binding as Bd
+    from paper_2402_13259_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, warm):
+        warm()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def emit(row, units, ms, base_ms, cfg, entry, parity):
+        line = {"metric": f"{row}: station-step updates/s", "impl": "ours", "row": row,
+                "value": units / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
+                "relative_to_simulate": (base_ms / ms) if base_ms else None, "steps": args.steps,
+                "n_gpus": 1, "dtype": "f32", "data": "synthetic", "entry_point": entry,
+                "parity_tests": parity, "config": cfg}
+        print(json.dumps(line), flush=True)
+
+    run = W.layered_dag()
+    n, R, dt, T, seed = run.net.n, run.R, run.dt, run.T, run.seed
+    K = Bd.num_steps(dt, T)
+    units = n * K * R
+    cfg = {"workload": f"dag100: 100-station layered DAG, R={R}, T={T:g}, dt={dt:g} (K={K})"}
+    stats = torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda")
+    h = Bd.EulerNet(run.net)
+    base = {}
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        base[scheme] = timed(lambda: h.simulate(scheme, dt, T, R, seed, stats=stats, check=False),
+                             lambda: h.simulate(scheme, dt, T, 64, seed, check=False))
+        emit(f"simulate_{name}", units, base[scheme], base[scheme], cfg, "euler_net_simulate",
+             "tests/test_gpu_parity.py")
+    h.status()
+    # f1: average scheme (both schemes + the average, 2 units per station-step)
+    avg = torch.empty(Bd.stats_len(n, R), dtype=torch.float64, device="cuda")
+    sb = torch.empty_like(stats)
+    sf = torch.empty_like(stats)
+    L = Bd.lib()
+
+    def average(RR, out, b, f):
+        Bd._check(L.euler_net_simulate_average(h._h, dt, T, RR, seed, 0, Bd.C.c_void_p(out.data_ptr()),
+                                               Bd.C.c_void_p(b.data_ptr()), Bd.C.c_void_p(f.data_ptr()),
+                                               Bd.C.c_void_p(stream.cuda_stream)))
+    ms = timed(lambda: average(R, avg, sb, sf), lambda: average(64, avg, sb, sf))
+    emit("f1_average_scheme", 2 * units, ms, base[0] + base[1], cfg, "euler_net_simulate_average",
+         "tests/test_gpu_extensions.py")
+    # f2: sojourn times, 4 tagged customers per replication entering station 0 at t = 50
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        out = torch.empty((R, 4), dtype=torch.int32, device="cuda")
+        ms = timed(lambda: h.sojourn(scheme, dt, T, R, seed, 0, K // 2, 4, out=out, stats=stats, check=False),
+                   lambda: h.sojourn(scheme, dt, T, 64, seed, 0, K // 2, 4, check=False))
+        c = dict(cfg, tagged="4 per replication, station 0, entry step K/2")
+        emit(f"f2_sojourn_{name}", units, ms, base[scheme], c, "euler_net_sojourn",
+             "tests/test_gpu_sojourn.py")
+    h.status()
+    # f4: Eq. (1) and Eq. (2) departure samplers
+    for mode in (1, 2):
+        h.set_option(Bd.OPT_DEPARTURE, mode)
+        for scheme, name in ((0, "backward"), (1, "forward")):
+            ms = timed(lambda: h.simulate(scheme, dt, T, R, seed, stats=stats, check=False),
+                       lambda: h.simulate(scheme, dt, T, 64, seed, check=False))
+            emit(f"f4_eq{mode}_departures_{name}", units, ms, base[scheme], cfg, "euler_net_simulate",
+                 "tests/test_gpu_extensions.py")
+    h.set_option(Bd.OPT_DEPARTURE, 0)
+    h.status()
+    h.close()
+    # f3: staffing schedule, m_i(t) = m_i x (1, 1.1, 0.9, 1.2) over 25-unit intervals
+    net = run.net
+    fac = np.array([1.0, 1.1, 0.9, 1.2])
+    net.servers_schedule = np.maximum(1, np.round(fac[:, None] * net.servers[None, :])).astype(np.int32)
+    net.servers_schedule_dt = 25.0
+    hs = Bd.EulerNet(net)
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        ms = timed(lambda: hs.simulate(scheme, dt, T, R, seed, stats=stats, check=False),
+                   lambda: hs.simulate(scheme, dt, T, 64, seed, check=False))
+        emit(f"f3_staffing_schedule_{name}", units, ms, base[scheme],
+             dict(cfg, schedule="m_i x (1, 1.1, 0.9, 1.2) per 25 time units"), "euler_net_simulate",
+             "tests/test_gpu_extensions.py")
+    hs.status()
+    hs.close()
+    net.servers_schedule = None
+    # C4: likelihood-ratio gradients
+    g = W.sinusoid_dag()
+    hg = Bd.EulerNet(g.net)
+    Kg = Bd.num_steps(g.dt, g.T)
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        ms = timed(lambda: hg.grad(scheme, g.dt, g.T, g.R, g.seed, check=False),
+                   lambda: hg.grad(scheme, g.dt, g.T, 64, g.seed, check=False))
+        emit(f"c4_gradient_{name}", g.net.n * Kg * g.R, ms, None,
+             {"workload": f"dag100 with sinusoid arrivals, R={g.R}, T={g.T:g}, dt={g.dt:g}",
+              "gradient": "d/d(mu_1..mu_100, a, b, phase) of dt sum N and sum D"},
+             "euler_net_grad", "tests/test_gpu_grad.py")
+    hg.status()
+    hg.close()
+    # C2: staffing-scale sweep (2,000 stations), reduced replications
+    for sc in (10, 100, 1000, 10000):
+        rs = W.scale_dag(sc, R=2048)
+        hc = Bd.EulerNet(rs.net)
+        Ks = Bd.num_steps(rs.dt, rs.T)
+        st2 = torch.empty(Bd.stats_len(rs.net.n, rs.R), dtype=torch.int64, device="cuda")
+        for scheme, name in ((0, "backward"), (1, "forward")):
+            ms = timed(lambda: hc.simulate(scheme, rs.dt, rs.T, rs.R, rs.seed, stats=st2, check=False),
+                       lambda: hc.simulate(scheme, rs.dt, rs.T, 32, rs.seed, check=False))
+            emit(f"c2_scale_s{sc}_{name}", rs.net.n * Ks * rs.R, ms, None,
+                 {"workload": f"20x100 layered DAG, s={sc}, dt={rs.dt:.4g}, T={rs.T:g} (K={Ks}), R={rs.R}",
+                  "plan": hc.plan(scheme, rs.R)},
+                 "euler_net_simulate", "tests/test_gpu_parity.py")
+        hc.status()
+        hc.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -240,7 +404,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="dag100", choices=["dag100", "batch512"])
+    ap.add_argument("--workload", default="dag100", choices=["dag100", "batch512", "rows"])
     ap.add_argument("--batch-T-scale", type=float, default=0.1)
     ap.add_argument("--batch-R-scale", type=float, default=0.02)
     ap.add_argument("--replications", type=int, default=0,
@@ -251,6 +415,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch_comparison(args)
+    if args.workload == "rows":
+        return run_rows(args)
 
     import torch
     import torch.distributed as dist
@@ -334,6 +500,9 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.steps
         e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 2 * 8 * Bd.stats_len(n, R)}
+    plans = {"backward": h.plan(0, R), "forward": h.plan(1, R)}
+    L = num_levels(run.net)
+    launches = {name: launches_per_call(plans[name], sc, K, L) for sc, name in ((0, "backward"), (1, "forward"))}
     h.close()
 
     if rank != 0:
@@ -352,11 +521,16 @@ def main():
         achieved = sum(ops) / (sum(kern_ms) / 1e3)
         sm_max = clk.get("sm_max_mhz") or 2070.0
         peak = SMS * LANES_PER_SM * sm_max * 1e6
-        valid = TRAFFIC["hash"] == kernel_hash()
+        valid = TRAFFIC["hash"] == kernel_hash() and TRAFFIC.get("forms") == [plans["backward"]["form"],
+                                                                             plans["forward"]["form"]]
+        hbm = plans["backward"]["form"] == 2
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak,
-                "traffic": TRAFFIC["bytes_per_launch"] if valid else None,
-                "kernel": "persistent_kernel", "ops_per_unit": {k: v["ops_per_unit"] for k, v in per_scheme.items()},
+                "traffic": TRAFFIC["bytes_per_call"] if valid else None,
+                "kernel": "hbm_phase_kernel (per-step kernels of one simulate call, CUDA graph)" if hbm
+                          else "persistent_kernel",
+                "launch": "one euler_net_simulate call per scheme (kernel time + graph launch gaps)",
+                "ops_per_unit": {k: v["ops_per_unit"] for k, v in per_scheme.items()},
                 "peak_note": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz (issue rate)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -366,8 +540,8 @@ def main():
         "per_scheme": {"backward": {"ms_per_launch": kern_ms[0], "value": units_launch / (kern_ms[0] / 1e3)},
                        "forward": {"ms_per_launch": kern_ms[1], "value": units_launch / (kern_ms[1] / 1e3)}},
         "roofline": roof, "cpu_baseline": base, "e2e": e2e, "clocks": clk,
-        "gpu_launches": 2 * args.steps,
-        "plan": {"backward": Bd.EulerNet(run.net).plan(0, R), "forward": Bd.EulerNet(run.net).plan(1, R)},
+        "gpu_launches": (launches["backward"] + launches["forward"]) * args.steps,
+        "plan": plans,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

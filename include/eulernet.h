@@ -274,10 +274,15 @@ EULERNET_API int euler_net_status(euler_net* net, void* cuda_stream);
 /* Tuning and testing options (see EULER_OPT_*); value < 0 restores the
  * default.  Returns EULER_OK or EULER_ERR_ARG. */
 enum {
-  EULER_OPT_FORM = 0,        /* 0 = auto, 1 = persistent shared-memory kernel
-                                with block barriers, 2 = per-step kernels over
-                                HBM state (graph), 3 = level-pipelined
-                                shared-memory kernel                           */
+  EULER_OPT_FORM = 0,        /* 0 = auto (2 when n x replications >= 2^18,
+                                else 1; 2 also when a tile does not fit in
+                                shared memory), 1 = persistent shared-memory
+                                kernel with block barriers, 2 = per-step
+                                kernels over HBM state replayed from a CUDA
+                                graph (forward scheme: one skewed launch per
+                                step for all stations), 3 = level-pipelined
+                                shared-memory kernel.  All forms give the same
+                                results bit for bit.                           */
   EULER_OPT_TILE_REPS = 1,   /* replications per tile (power of two)           */
   EULER_OPT_BLOCK = 2,       /* threads per block                              */
   EULER_OPT_GRID = 3,        /* blocks of the persistent kernel (0 = auto)     */

@@ -199,6 +199,9 @@ bool make_pipe_plan(const euler_net* h, int W, PipePlan* pp) {
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Units per step (n R) from which the planner takes the HBM form.
+constexpr int64_t kHbmMinUnitsPerStep = int64_t(1) << 18;
+
 int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   const int64_t limit = h->smem_optin;
   const int forced_form = (int)h->opt[EULER_OPT_FORM];
@@ -238,6 +241,12 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
     if (forced_form == 3) return fail(EULER_ERR_TOO_LARGE, "pipelined form does not fit");
   }
   pl->form = (forced_form == 1 || forced_form == 2) ? forced_form : 1;
+  // With enough units in one step the HBM form wins: its per-step kernels
+  // balance the stations' uneven sampler work over the whole GPU, where the
+  // persistent form waits at block barriers every phase (forward: every
+  // level), and its state traffic (about 8 + 8 deg bytes per unit) stays far
+  // below HBM bandwidth.  Below the threshold launch gaps dominate.
+  if (forced_form <= 0 && (int64_t)h->n * R >= kHbmMinUnitsPerStep) pl->form = 2;
   if (pl->form == 1 && (Rt < 1 || persistent_smem_bytes(h->n, h->E, Rt) > limit)) {
     if (forced_form == 1) return fail(EULER_ERR_TOO_LARGE, "network tile does not fit in shared memory");
     pl->form = 2;
@@ -286,7 +295,31 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   return EULER_OK;
 }
 
+// Level of each station position of the level order, and the ring depth of
+// the skewed forward scheme: the largest level gap of an edge, plus one.
+int ensure_levels(euler_net* h) {
+  if (h->d_pos_level) return EULER_OK;
+  std::vector<int32_t> pos_level(h->n), level(h->n);
+  for (int32_t j = 0; j < h->L; ++j)
+    for (int32_t k = h->lvl_ptr[j]; k < h->lvl_ptr[j + 1]; ++k) {
+      pos_level[k] = j;
+      level[h->lvl_station[k]] = j;
+    }
+  int32_t gap = 0;
+  for (int32_t i = 0; i < h->n; ++i)
+    for (int32_t e = h->row_ptr[i]; e < h->row_ptr[i + 1]; ++e)
+      gap = std::max(gap, level[h->col[e]] - level[i]);
+  CUDA_TRY(cudaMalloc(&h->d_pos_level, sizeof(int32_t) * (size_t)h->n));
+  CUDA_TRY(cudaMemcpy(h->d_pos_level, pos_level.data(), sizeof(int32_t) * (size_t)h->n,
+                      cudaMemcpyHostToDevice));
+  h->h2d_bytes += (int64_t)sizeof(int32_t) * h->n;
+  h->hbm_depth = gap + 1;
+  return EULER_OK;
+}
+
 int ensure_hbm_state(euler_net* h, int64_t R) {
+  int rc = ensure_levels(h);
+  if (rc) return rc;
   const int64_t ld = (R + 3) / 4 * 4;
   if (ld <= h->hbm_cap_ld && R <= h->hbm_cap_R && h->d_N) return EULER_OK;
   cudaFree(h->d_N);
@@ -296,12 +329,17 @@ int ensure_hbm_state(euler_net* h, int64_t R) {
   h->d_Redge = nullptr;
   h->d_racc = nullptr;
   CUDA_TRY(cudaMalloc(&h->d_N, sizeof(int32_t) * (size_t)h->n * ld));
-  CUDA_TRY(cudaMalloc(&h->d_Redge, sizeof(int32_t) * (size_t)std::max(h->E, 1) * ld));
+  CUDA_TRY(cudaMalloc(&h->d_Redge,
+                      sizeof(int32_t) * (size_t)std::max(h->hbm_depth, 2) * std::max(h->E, 1) * ld));
   CUDA_TRY(cudaMalloc(&h->d_racc, sizeof(int64_t) * 4 * (size_t)std::max<int64_t>(R, 1)));
   if (!h->d_tau) CUDA_TRY(cudaMalloc(&h->d_tau, sizeof(int32_t)));
   h->hbm_cap_ld = ld;
   h->hbm_cap_R = R;
   return EULER_OK;
+}
+
+int64_t hbm_slots(const euler_net* h, int32_t scheme, int64_t K) {
+  return scheme == EULER_BACKWARD ? K + 1 : K + h->L - 1;
 }
 
 int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl, cudaStream_t s) {
@@ -313,15 +351,20 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   hs.racc = h->d_racc;
   hs.tau = h->d_tau;
   hs.ld = h->hbm_cap_ld;
+  hs.pos_level = h->d_pos_level;
+  hs.depth = h->hbm_depth;
   CUDA_TRY(launch_hbm_init(t, p, hs, s));
+  // backward: K + 1 fused slots; forward: K + L - 1 skewed slots
+  const int64_t slots = hbm_slots(h, p.scheme, p.K);
   const int64_t S = h->opt[EULER_OPT_GRAPH_STEPS] > 0 ? h->opt[EULER_OPT_GRAPH_STEPS]
-                                                      : std::min<int64_t>(p.K, 32);
+                                                      : std::min<int64_t>(slots, 32);
   if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int64_t k = 0; k < S; ++k) {
-    cudaError_t e = launch_hbm_step(t, p, hs, pl.block, h->lvl_ptr.data(), h->cap_stream);
+  for (int64_t k = 0; k <= S; ++k) {
+    cudaError_t e = k < S ? launch_hbm_slot(t, p, hs, pl.block, (int32_t)k, h->cap_stream)
+                          : launch_hbm_advance(hs, (int32_t)S, h->cap_stream);
     if (e != cudaSuccess) {
       cudaStreamEndCapture(h->cap_stream, &graph);
       if (graph) cudaGraphDestroy(graph);
@@ -332,7 +375,7 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  const int64_t replays = (p.K + S - 1) / S;
+  const int64_t replays = (slots + S - 1) / S;
   for (int64_t k = 0; k < replays && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
   cudaGraphExecDestroy(exec);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
@@ -423,6 +466,7 @@ void euler_net_destroy(euler_net* h) {
   cudaFree(h->d_muh);
   cudaFree(h->d_col);
   cudaFree(h->d_sstats);
+  cudaFree(h->d_pos_level);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }

@@ -62,8 +62,9 @@ struct euler_net {
   int32_t* d_col = nullptr;
   int64_t* d_sstats = nullptr;
   size_t sstats_cap = 0;
-  // HBM-form state
-  int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr;
+  // HBM-form state; Redge holds hbm_depth ring slots (skewed forward scheme)
+  int32_t *d_N = nullptr, *d_Redge = nullptr, *d_tau = nullptr, *d_pos_level = nullptr;
+  int32_t hbm_depth = 0;
   int64_t* d_racc = nullptr;
   int64_t hbm_cap_ld = 0, hbm_cap_R = 0;
   cudaStream_t cap_stream = nullptr;

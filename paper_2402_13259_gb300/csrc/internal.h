@@ -103,10 +103,13 @@ cudaError_t launch_pipeline(const NetTables& t, const RunParams& p, const PipePl
 // HBM-state form: per-step kernels over state in global memory.
 struct HbmState {
   int32_t* N;      // [n][R] station-major, replication-fastest
-  int32_t* Redge;  // [E][R]
+  int32_t* Redge;  // [max(depth, 2)][E][R]: routed counts of step tau in ring slot tau % depth
+                   // (forward skewed) or tau % 2 (backward fused)
   int64_t* racc;   // [R][4] per-replication partial sums
-  int32_t* tau;    // device step counter (1-based)
+  int32_t* tau;    // device step (or skewed-slot) counter, 1-based
   int64_t ld;      // leading dimension (>= R, multiple of 4)
+  const int32_t* pos_level = nullptr;  // [n] level of lvl_station[k] (skewed forward only)
+  int32_t depth = 1;                   // ring slots of Redge: max level gap of an edge + 1
 };
 int64_t hbm_smem_bytes(int32_t n, int32_t tile_reps);
 cudaError_t launch_hbm_init(const NetTables& t, const RunParams& p, const HbmState& hs,
@@ -115,6 +118,13 @@ cudaError_t launch_hbm_init(const NetTables& t, const RunParams& p, const HbmSta
 // step counter advance.  Safe to capture in a CUDA graph.
 cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
                             const int32_t* lvl_ptr_host, cudaStream_t s);
+// One captured slot of the HBM form at device counter + koff: backward, the
+// gather of step tau - 1 fused with the draws of step tau (slots 1 .. K+1);
+// forward, skewed slot tau (every station i runs its step tau - level(i) when
+// that lies in 1..K).  Does not advance the counter.
+cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
+                            int32_t koff, cudaStream_t s);
+cudaError_t launch_hbm_advance(const HbmState& hs, int32_t by, cudaStream_t s);
 cudaError_t launch_hbm_finish(const NetTables& t, const RunParams& p, const HbmState& hs,
                               cudaStream_t s);
 

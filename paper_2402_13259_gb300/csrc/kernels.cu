@@ -189,16 +189,29 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
 
 constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
 
-// Units of one phase over stations lvl_station[s0 .. s0+m) (or 0..n when
-// all == true).  Grid: x over replication tiles of 32, y over station chunks.
+// Units of one phase over stations lvl_station[s0 .. s0+m) (phases 2, 3) or
+// 0 .. m (phases 0, 1), at device counter + koff.  Grid: x over replication
+// tiles of 32, y over station chunks.
+//   0: backward departures / routing / arrivals of step tau (Algorithm 2)
+//   1: backward gather / update of step tau
+//   2: forward units of one level of step tau (Algorithm 3)
+//   4: backward, fused slot tau (1 .. K+1): the gather / update of step
+//      tau - 1 (routed counts of the previous launch, ring slot (tau-1) % 2),
+//      then the departures / routing / arrivals of step tau from that N_{tau-1}
+//      (ring slot tau % 2): one launch per step instead of two
+//   3: forward, skewed slot tau: station i at level l runs step tau - l.  Its
+//      predecessors (lower levels) ran that step in earlier slots and its own
+//      previous step in the previous slot, so every dependency of Algorithm 3
+//      is met with one launch per slot for all stations; routed counts of
+//      step s live in ring slot s % depth until their consumer has read them.
 template <int PHASE>
 __global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
-                                                           int32_t s0, int32_t m) {
+                                                           int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
   __shared__ float rinv[64];
   __shared__ long long racc_s[kHbmTile * 4];
-  const int32_t tau = *hs.tau;
-  if (tau > p.K) return;  // uniform: steps past the horizon are no-ops
+  const int32_t slot = *hs.tau + koff;
+  if (slot > (phase == 3 ? p.K + t.L - 1 : phase == 4 ? p.K + 1 : p.K)) return;  // uniform
   const int tid = threadIdx.x;
   fill_rinv(rinv);
   for (int k = tid; k < kHbmTile * 4; k += blockDim.x) racc_s[k] = 0;
@@ -207,40 +220,66 @@ __global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParam
   const int G = blockDim.x / kHbmTile;
   const int su = blockIdx.y * G + tid / kHbmTile;
   const int64_t rloc = (int64_t)blockIdx.x * kHbmTile + r;
-  const bool act = rloc < p.R && su < m;
+  int32_t tau = slot;
+  bool live = su < m;  // this warp's station has a step in this slot
+  int32_t* redge = hs.Redge;
+  if (phase == 3) {
+    tau = slot - (su < m ? __ldg(hs.pos_level + s0 + su) : 0);
+    live = live && tau >= 1 && tau <= p.K;
+    if (live) redge = hs.Redge + (int64_t)(tau % hs.depth) * t.E * hs.ld;
+  }
+  const bool act = rloc < p.R && live;
   const bool lead = (tid & 31) == 0;
-  const int32_t i = su < m ? (phase == 2 ? __ldg(t.lvl_station + s0 + su) : su) : 0;
+  const int32_t i = su < m ? (phase >= 2 ? __ldg(t.lvl_station + s0 + su) : su) : 0;
   const uint32_t rep = (uint32_t)(p.rep_begin + rloc);
-  const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
+  const float* lam_t = p.lam + (int64_t)(live && tau <= p.K ? tau - 1 : 0) * t.n_ex;
   SamplerCtx cx{rinv, p.cap, 0u};
   long long* st = reinterpret_cast<long long*>(p.stats + 5 * (int64_t)i);
   int32_t part[4] = {0, 0, 0, 0};  // Q, D, X, A per replication
   if constexpr (phase == 0) {  // backward departures / routing / arrivals
     int32_t v[3] = {0, 0, 0};
     if (act) {
-      const UnitOut o = unit_update<false>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
+      const UnitOut o = unit_update<false>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
       v[0] = o.D; v[1] = o.X; v[2] = o.A;
       part[1] = o.D; part[2] = o.X; part[3] = o.A;
     }
-    reduce_to<3>(st + 2, v, lead && su < m, 32, true);
+    reduce_to<3>(st + 2, v, lead && live, 32, true);
   } else if constexpr (phase == 1) {  // backward gather / update
     int32_t v[2] = {0, 0};
     if (act) {
-      const int32_t nn = backward_gather(t, i, hs.N, hs.Redge, hs.ld, rloc, cx.err);
+      const int32_t nn = backward_gather(t, i, hs.N, redge, hs.ld, rloc, cx.err);
       const int32_t c = servers_at(t, p, i, (uint32_t)tau);
       v[0] = nn; v[1] = nn < c ? nn : c;
       part[0] = nn;
     }
-    reduce_to<2>(st, v, lead && su < m, 32, true);
-  } else {  // forward level
+    reduce_to<2>(st, v, lead && live, 32, true);
+  } else if constexpr (phase == 4) {  // backward, fused: gather tau - 1, then draw tau
     int32_t v[5] = {0, 0, 0, 0, 0};
     if (act) {
-      const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, hs.Redge, hs.ld, rloc, cx);
+      if (slot >= 2) {
+        const int32_t* rprev = hs.Redge + (int64_t)((slot - 1) & 1) * t.E * hs.ld;
+        const int32_t nn = backward_gather(t, i, hs.N, rprev, hs.ld, rloc, cx.err);
+        const int32_t c = servers_at(t, p, i, (uint32_t)(slot - 1));
+        v[0] = nn; v[1] = nn < c ? nn : c;
+        part[0] = nn;
+      }
+      if (slot <= p.K) {
+        int32_t* rcur = hs.Redge + (int64_t)(slot & 1) * t.E * hs.ld;
+        const UnitOut o = unit_update<false>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx);
+        v[2] = o.D; v[3] = o.X; v[4] = o.A;
+        part[1] = o.D; part[2] = o.X; part[3] = o.A;
+      }
+    }
+    reduce_to<5>(st, v, lead && live, 32, true);
+  } else {  // forward: one level (2) or a skewed slot (3)
+    int32_t v[5] = {0, 0, 0, 0, 0};
+    if (act) {
+      const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
       const int32_t c = servers_at(t, p, i, (uint32_t)tau);
       v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
       part[0] = o.N; part[1] = o.D; part[2] = o.X; part[3] = o.A;
     }
-    reduce_to<5>(st, v, lead && su < m, 32, true);
+    reduce_to<5>(st, v, lead && live, 32, true);
   }
   if (act) {
 #pragma unroll
@@ -258,7 +297,7 @@ __global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParam
   latch(p.err, cx.err);
 }
 
-__global__ void hbm_advance_kernel(int32_t* tau) { *tau += 1; }
+__global__ void hbm_advance_kernel(int32_t* tau, int32_t by) { *tau += by; }
 
 __global__ void hbm_init_kernel(NetTables t, RunParams p, HbmState hs) {
   const int64_t total = (int64_t)t.n * hs.ld;
@@ -424,16 +463,34 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
   const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
   if (p.scheme == 0) {
     dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
-    hbm_phase_kernel<0><<<grid, block, 0, s>>>(t, p, hs, 0, t.n);
-    hbm_phase_kernel<1><<<grid, block, 0, s>>>(t, p, hs, 0, t.n);
+    hbm_phase_kernel<0><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, 0);
+    hbm_phase_kernel<1><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, 0);
   } else {
     for (int32_t j = 0; j < t.L; ++j) {
       const int32_t s0 = lvl_ptr_host[j], m = lvl_ptr_host[j + 1] - lvl_ptr_host[j];
       dim3 grid(tiles, (unsigned)((m + G - 1) / G));
-      hbm_phase_kernel<2><<<grid, block, 0, s>>>(t, p, hs, s0, m);
+      hbm_phase_kernel<2><<<grid, block, 0, s>>>(t, p, hs, s0, m, 0);
     }
   }
-  hbm_advance_kernel<<<1, 1, 0, s>>>(hs.tau);
+  hbm_advance_kernel<<<1, 1, 0, s>>>(hs.tau, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
+                            int32_t koff, cudaStream_t s) {
+  const int G = block / kHbmTile;
+  const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
+  dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
+  if (p.scheme == 0) {
+    hbm_phase_kernel<4><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+  } else {
+    hbm_phase_kernel<3><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_advance(const HbmState& hs, int32_t by, cudaStream_t s) {
+  hbm_advance_kernel<<<1, 1, 0, s>>>(hs.tau, by);
   return cudaGetLastError();
 }
 

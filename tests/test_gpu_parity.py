@@ -63,13 +63,16 @@ def test_tandem_full_parity(Bd, orc, scheme):
     _invariants(Bd, got, run.net, run.R)
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_dag100_full_size_sampled(Bd, orc, scheme):
+def test_dag100_full_size_sampled(Bd, orc, scheme, form):
     """100-station layered DAG at full size (10,000 replications x 10,000
-    steps, the benchmark's launch): sampled replications re-run by the oracle
-    must match exactly; invariants over all replications."""
+    steps; form 0 = the planner's choice, the benchmark's launch, and the
+    persistent form): sampled replications re-run by the oracle must match
+    exactly; invariants over all replications."""
     run = W.layered_dag()
-    got = _gpu_stats(Bd, run.net, scheme, run.dt, run.T, run.R, run.seed)
+    got = _gpu_stats(Bd, run.net, scheme, run.dt, run.T, run.R, run.seed,
+                     options={Bd.OPT_FORM: form} if form else None)
     _invariants(Bd, got, run.net, run.R)
     rng = np.random.default_rng(123)
     reps = sorted({0, 1, 31, 32, 5000, run.R - 1} | set(rng.integers(0, run.R, 4).tolist()))
@@ -106,6 +109,20 @@ def test_small_networks_parity(Bd, orc, case, scheme):
     got = _gpu_stats(Bd, net, scheme, dt, T, R, 1000 + case)
     want = orc.simulate(net, scheme, dt, T, R, 1000 + case)["stats"]
     _assert_equal(got, want, f"case {case} scheme {scheme}")
+
+
+@pytest.mark.parametrize("case", range(7))
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_small_networks_hbm_form_parity(Bd, orc, case, scheme):
+    """The HBM form on the same cases: skip edges across several levels make
+    the skewed forward scheme keep routed counts for more than one step
+    (ring depth > 2); one and five steps per graph replay."""
+    net, R, dt, T = _small_cases()[case]
+    want = orc.simulate(net, scheme, dt, T, R, 1000 + case)["stats"]
+    for steps in (1, 5):
+        got = _gpu_stats(Bd, net, scheme, dt, T, R, 1000 + case,
+                         options={Bd.OPT_FORM: 2, Bd.OPT_GRAPH_STEPS: steps})
+        _assert_equal(got, want, f"hbm case {case} scheme {scheme} graph steps {steps}")
 
 
 @pytest.mark.parametrize("scheme", [0, 1])
