@@ -284,7 +284,7 @@ enum {
                                 shared-memory kernel.  All forms give the same
                                 results bit for bit.                           */
   EULER_OPT_TILE_REPS = 1,   /* replications per tile (power of two)           */
-  EULER_OPT_BLOCK = 2,       /* threads per block                              */
+  EULER_OPT_BLOCK = 2,       /* threads per block (HBM form: default 256)      */
   EULER_OPT_GRID = 3,        /* blocks of the persistent kernel (0 = auto)     */
   EULER_OPT_SAMPLER_CAP = 4, /* rejection-loop iteration cap (default 1000)    */
   EULER_OPT_GRAPH_STEPS = 5, /* steps captured per CUDA graph (HBM form)       */

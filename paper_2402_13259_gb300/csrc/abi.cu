@@ -199,8 +199,10 @@ bool make_pipe_plan(const euler_net* h, int W, PipePlan* pp) {
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// Units per step (n R) from which the planner takes the HBM form.
+// Units per step (n R) from which the planner takes the HBM form, and its
+// default threads per block.
 constexpr int64_t kHbmMinUnitsPerStep = int64_t(1) << 18;
+constexpr int kHbmBlock = 256;
 
 int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   const int64_t limit = h->smem_optin;
@@ -253,7 +255,7 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   }
   if (pl->form == 2) {
     pl->tile_reps = 32;
-    pl->block = h->opt[EULER_OPT_BLOCK] > 0 ? (int)h->opt[EULER_OPT_BLOCK] : 256;
+    pl->block = h->opt[EULER_OPT_BLOCK] > 0 ? (int)h->opt[EULER_OPT_BLOCK] : kHbmBlock;
     if (pl->block % 32 || pl->block > 256) return fail(EULER_ERR_ARG, "HBM-form block must be a multiple of 32 <= 256");
     pl->grid = 0;
     pl->smem = 0;
@@ -285,7 +287,7 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
     if (forced_form == 1) return fail(EULER_ERR_TOO_LARGE, "persistent kernel cannot be resident");
     pl->form = 2;
     pl->tile_reps = 32;
-    pl->block = 256;
+    pl->block = kHbmBlock;
     pl->num_tiles = (R + 31) / 32;
     return EULER_OK;
   }

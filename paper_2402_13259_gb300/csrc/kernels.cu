@@ -190,109 +190,110 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
 constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
 
 // Units of one phase over stations lvl_station[s0 .. s0+m) (phases 2, 3) or
-// 0 .. m (phases 0, 1), at device counter + koff.  Grid: x over replication
-// tiles of 32, y over station chunks.
+// 0 .. m (phases 0, 1, 4), at device counter + koff.  Grid: x over
+// replication tiles of 32, y over station chunks; one warp per station and
+// tile.
 //   0: backward departures / routing / arrivals of step tau (Algorithm 2)
 //   1: backward gather / update of step tau
-//   2: forward units of one level of step tau (Algorithm 3)
 //   4: backward, fused slot tau (1 .. K+1): the gather / update of step
 //      tau - 1 (routed counts of the previous launch, ring slot (tau-1) % 2),
 //      then the departures / routing / arrivals of step tau from that N_{tau-1}
 //      (ring slot tau % 2): one launch per step instead of two
+//   2: forward units of one level of step tau (Algorithm 3)
 //   3: forward, skewed slot tau: station i at level l runs step tau - l.  Its
 //      predecessors (lower levels) ran that step in earlier slots and its own
 //      previous step in the previous slot, so every dependency of Algorithm 3
 //      is met with one launch per slot for all stations; routed counts of
 //      step s live in ring slot s % depth until their consumer has read them.
-template <int PHASE>
+// Warps never wait for one another: each keeps its own 1/k table, adds its
+// station sums with one warp reduction and its per-replication sums with one
+// atomic per value, so a warp whose station drew cheap samples leaves at once.
+template <int PHASE, bool EXT = true>
 __global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
                                                            int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
-  __shared__ float rinv[64];
-  __shared__ long long racc_s[kHbmTile * 4];
+  __shared__ float rinv_s[8 * 64];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rinv = rinv_s + 64 * wib;
+  for (int k = lane; k < 64; k += 32) rinv[k] = k ? 1.0f / (float)k : 0.0f;
+  __syncwarp();
   const int32_t slot = *hs.tau + koff;
   if (slot > (phase == 3 ? p.K + t.L - 1 : phase == 4 ? p.K + 1 : p.K)) return;  // uniform
-  const int tid = threadIdx.x;
-  fill_rinv(rinv);
-  for (int k = tid; k < kHbmTile * 4; k += blockDim.x) racc_s[k] = 0;
-  __syncthreads();
-  const int r = tid % kHbmTile;
-  const int G = blockDim.x / kHbmTile;
-  const int su = blockIdx.y * G + tid / kHbmTile;
-  const int64_t rloc = (int64_t)blockIdx.x * kHbmTile + r;
-  int32_t tau = slot;
-  bool live = su < m;  // this warp's station has a step in this slot
-  int32_t* redge = hs.Redge;
-  if (phase == 3) {
-    tau = slot - (su < m ? __ldg(hs.pos_level + s0 + su) : 0);
-    live = live && tau >= 1 && tau <= p.K;
-    if (live) redge = hs.Redge + (int64_t)(tau % hs.depth) * t.E * hs.ld;
-  }
-  const bool act = rloc < p.R && live;
-  const bool lead = (tid & 31) == 0;
-  const int32_t i = su < m ? (phase >= 2 ? __ldg(t.lvl_station + s0 + su) : su) : 0;
+  const int64_t rloc = (int64_t)blockIdx.x * kHbmTile + lane;
+  const bool rok = rloc < p.R;
   const uint32_t rep = (uint32_t)(p.rep_begin + rloc);
-  const float* lam_t = p.lam + (int64_t)(live && tau <= p.K ? tau - 1 : 0) * t.n_ex;
+  const int su = blockIdx.y * (blockDim.x >> 5) + wib;
+  if (su >= m) return;  // uniform across the warp; no block barrier follows
+  const bool lead = lane == 0;
   SamplerCtx cx{rinv, p.cap, 0u};
-  long long* st = reinterpret_cast<long long*>(p.stats + 5 * (int64_t)i);
-  int32_t part[4] = {0, 0, 0, 0};  // Q, D, X, A per replication
-  if constexpr (phase == 0) {  // backward departures / routing / arrivals
-    int32_t v[3] = {0, 0, 0};
-    if (act) {
-      const UnitOut o = unit_update<false>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
-      v[0] = o.D; v[1] = o.X; v[2] = o.A;
-      part[1] = o.D; part[2] = o.X; part[3] = o.A;
+  int32_t part[4] = {0, 0, 0, 0};  // Q, D, X, A of this lane's replication
+  {
+    const int32_t i = phase == 2 || phase == 3 ? __ldg(t.lvl_station + s0 + su) : su;
+    int32_t tau = slot;
+    bool live = true;  // this station has a step in this slot
+    int32_t* redge = hs.Redge;
+    if (phase == 3) {
+      tau = slot - __ldg(hs.pos_level + s0 + su);
+      live = tau >= 1 && tau <= p.K;
+      if (!live) return;  // uniform across the warp
+      redge = hs.Redge + (int64_t)(tau % hs.depth) * t.E * hs.ld;
     }
-    reduce_to<3>(st + 2, v, lead && live, 32, true);
-  } else if constexpr (phase == 1) {  // backward gather / update
-    int32_t v[2] = {0, 0};
-    if (act) {
-      const int32_t nn = backward_gather(t, i, hs.N, redge, hs.ld, rloc, cx.err);
-      const int32_t c = servers_at(t, p, i, (uint32_t)tau);
-      v[0] = nn; v[1] = nn < c ? nn : c;
-      part[0] = nn;
-    }
-    reduce_to<2>(st, v, lead && live, 32, true);
-  } else if constexpr (phase == 4) {  // backward, fused: gather tau - 1, then draw tau
-    int32_t v[5] = {0, 0, 0, 0, 0};
-    if (act) {
-      if (slot >= 2) {
-        const int32_t* rprev = hs.Redge + (int64_t)((slot - 1) & 1) * t.E * hs.ld;
-        const int32_t nn = backward_gather(t, i, hs.N, rprev, hs.ld, rloc, cx.err);
-        const int32_t c = servers_at(t, p, i, (uint32_t)(slot - 1));
+    const bool act = rok && live;
+    const float* lam_t = p.lam + (int64_t)(tau <= p.K ? tau - 1 : 0) * t.n_ex;
+    long long* st = reinterpret_cast<long long*>(p.stats + 5 * (int64_t)i);
+    if constexpr (phase == 0) {  // backward departures / routing / arrivals
+      int32_t v[3] = {0, 0, 0};
+      if (act) {
+        const UnitOut o = unit_update<false, false, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
+        v[0] = o.D; v[1] = o.X; v[2] = o.A;
+        part[1] += o.D; part[2] += o.X; part[3] += o.A;
+      }
+      reduce_to<3>(st + 2, v, lead, 32, true);
+    } else if constexpr (phase == 1) {  // backward gather / update
+      int32_t v[2] = {0, 0};
+      if (act) {
+        const int32_t nn = backward_gather(t, i, hs.N, redge, hs.ld, rloc, cx.err);
+        const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
         v[0] = nn; v[1] = nn < c ? nn : c;
-        part[0] = nn;
+        part[0] += nn;
       }
-      if (slot <= p.K) {
-        int32_t* rcur = hs.Redge + (int64_t)(slot & 1) * t.E * hs.ld;
-        const UnitOut o = unit_update<false>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx);
-        v[2] = o.D; v[3] = o.X; v[4] = o.A;
-        part[1] = o.D; part[2] = o.X; part[3] = o.A;
+      reduce_to<2>(st, v, lead, 32, true);
+    } else if constexpr (phase == 4) {  // backward, fused: gather tau - 1, then draw tau
+      int32_t v[5] = {0, 0, 0, 0, 0};
+      if (act) {
+        if (slot >= 2) {
+          const int32_t* rprev = hs.Redge + (int64_t)((slot - 1) & 1) * t.E * hs.ld;
+          const int32_t nn = backward_gather(t, i, hs.N, rprev, hs.ld, rloc, cx.err);
+          const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)(slot - 1));
+          v[0] = nn; v[1] = nn < c ? nn : c;
+          part[0] += nn;
+        }
+        if (slot <= p.K) {
+          int32_t* rcur = hs.Redge + (int64_t)(slot & 1) * t.E * hs.ld;
+          const UnitOut o = unit_update<false, false, EXT>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx);
+          v[2] = o.D; v[3] = o.X; v[4] = o.A;
+          part[1] += o.D; part[2] += o.X; part[3] += o.A;
+        }
       }
+      reduce_to<5>(st, v, lead, 32, true);
+    } else {  // forward: one level (2) or a skewed slot (3)
+      int32_t v[5] = {0, 0, 0, 0, 0};
+      if (act) {
+        const UnitOut o = unit_update<true, false, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
+        const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
+        v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
+        part[0] += o.N; part[1] += o.D; part[2] += o.X; part[3] += o.A;
+      }
+      reduce_to<5>(st, v, lead, 32, true);
     }
-    reduce_to<5>(st, v, lead && live, 32, true);
-  } else {  // forward: one level (2) or a skewed slot (3)
-    int32_t v[5] = {0, 0, 0, 0, 0};
-    if (act) {
-      const UnitOut o = unit_update<true>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
-      const int32_t c = servers_at(t, p, i, (uint32_t)tau);
-      v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
-      part[0] = o.N; part[1] = o.D; part[2] = o.X; part[3] = o.A;
-    }
-    reduce_to<5>(st, v, lead && live, 32, true);
   }
-  if (act) {
+  if (rok) {
 #pragma unroll
     for (int s = 0; s < 4; ++s)
       if (part[s])
-        atomicAdd(reinterpret_cast<unsigned long long*>(racc_s + 4 * r + s), (unsigned long long)part[s]);
-  }
-  __syncthreads();
-  for (int k = tid; k < kHbmTile * 4; k += blockDim.x) {
-    const int64_t rr = (int64_t)blockIdx.x * kHbmTile + k / 4;
-    if (rr < p.R && racc_s[k] != 0)
-      atomicAdd(reinterpret_cast<unsigned long long*>(hs.racc + rr * 4 + (k & 3)),
-                (unsigned long long)racc_s[k]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(hs.racc + rloc * 4 + s),
+                  (unsigned long long)(long long)part[s]);
   }
   latch(p.err, cx.err);
 }
@@ -478,13 +479,20 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
 
 cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
                             int32_t koff, cudaStream_t s) {
-  const int G = block / kHbmTile;
+  const int G = block / kHbmTile;  // stations per block
   const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
   dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
+  const bool ext = p.mtab != nullptr || p.dep_mode != 0;
   if (p.scheme == 0) {
-    hbm_phase_kernel<4><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+    if (ext)
+      hbm_phase_kernel<4, true><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+    else
+      hbm_phase_kernel<4, false><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
   } else {
-    hbm_phase_kernel<3><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+    if (ext)
+      hbm_phase_kernel<3, true><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+    else
+      hbm_phase_kernel<3, false><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
   }
   return cudaGetLastError();
 }
