@@ -38,7 +38,10 @@ LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
 # DRAM bytes of one simulate call (mean of the two schemes) from ncu counters
 # (profiles/), valid only for the kernel sources with this hash and the launch
 # forms listed; reported as null otherwise.
-TRAFFIC = {"hash": None, "forms": None, "bytes_per_call": None}
+# profiles/hbm_phase_kernel_dag100.md: 11.945 MB (fused backward) and 11.948 MB
+# (skewed forward) DRAM bytes per step launch at steady state, x 10,001 and
+# 10,009 step launches per call.
+TRAFFIC = {"hash": "ba21facf351e998e", "forms": [2, 2], "bytes_per_call": 0.5 * (11.945e6 * 10001 + 11.948e6 * 10009)}
 
 
 def kernel_hash() -> str:
