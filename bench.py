@@ -175,9 +175,18 @@ def cpu_baseline(run, K_full, reps=12):
                             "philox_blocks_per_unit": c["philox_blocks"] / max(c["units"], 1)}
         total_units += units
         total_t += dt
+    # the exact event-by-event simulation of the same network, same box, same run
+    des_reps = 4
+    t0 = time.perf_counter()
+    d = O.des_simulate(run.net, run.dt, run.T, des_reps, run.seed)
+    des_t = time.perf_counter() - t0
+    des = {"value": run.net.n * K_full * des_reps / des_t, "unit": UNIT + " (grid-equivalent)",
+           "events_per_s": d["events"] / des_t, "cores": 1, "kind": "exact DES",
+           "sample": f"{des_reps} replications over T={run.T:g} (the Euler grid's {K_full} observation "
+                     f"times), single-threaded C", "seconds": des_t}
     return {"value": total_units / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} replications x {K_full} steps x {run.net.n} stations, both schemes "
-                      f"(single-threaded C oracle)", "seconds": total_t}, per_scheme
+                      f"(single-threaded C oracle)", "seconds": total_t, "des": des}, per_scheme
 
 
 def run_reference(args):

@@ -12,7 +12,7 @@
  *
  * Passages followed (section / algorithm / equation of the paper):
  *   - external arrivals: Sec. 2.1.1 (aggregated Poisson counts over a step)
- *   - pure-departure sampler: Lemma 1 and Algorithm 1 (Sec. 3.1)
+ *   - pure-departure sampler: Lemma 1 and Algorithm 1 (Sec. 4.1.3)
  *   - routing: Sec. 2.2 (multinomial split of a node's departures)
  *   - backward scheme: Sec. 2.2 task list 1-4 and Algorithm 2
  *   - forward scheme: Sec. 2.2 task list 1-4 and Algorithm 3 (node-by-node in

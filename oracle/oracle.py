@@ -19,12 +19,12 @@ __all__ = [
     "build_oracle", "lib", "simulate", "num_steps", "stats_split", "philox", "map_f32",
     "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
     "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
-    "BACKWARD", "FORWARD", "grad", "set_departure_mode", "sojourn", "sojourn_pstay",
+    "BACKWARD", "FORWARD", "grad", "set_departure_mode", "sojourn", "sojourn_pstay", "des_simulate",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.environ.get("EULER_ORACLE_SO") or os.path.join(HERE, "liboracle.so")
-SOURCES = [os.path.join(HERE, "euler_oracle.c")]
+SOURCES = [os.path.join(HERE, "euler_oracle.c"), os.path.join(HERE, "exact_des.c")]
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
           "-Wall", "-Wno-unused-function"]
 
@@ -42,7 +42,8 @@ COUNTER_NAMES = [
 def build_oracle(force: bool = False) -> str:
     if os.environ.get("EULER_ORACLE_SO"):
         return SO_PATH  # a prebuilt variant (used by the mutation test)
-    newest = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "euler_oracle.h")])
+    newest = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "euler_oracle.h"),
+                                                          os.path.join(HERE, "exact_des.h")])
     if force or not os.path.exists(SO_PATH) or os.path.getmtime(SO_PATH) < newest:
         tmp = SO_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *SOURCES, "-lm"])
@@ -93,6 +94,8 @@ def lib():
         L.eo_set_departure_mode.restype = C.c_int32
         L.eo_set_departure_mode.argtypes = [C.c_int32]
         L.eo_grad.restype = C.c_int
+        L.eo_des_simulate.argtypes = [C.POINTER(_Net), C.c_double, C.c_double, C.c_int64, C.c_uint64,
+                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
         L.eo_sojourn.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
                                  C.c_uint64, C.c_int64, C.c_int32, C.c_int64, C.c_int32,
                                  C.c_void_p, C.c_void_p]
@@ -214,6 +217,29 @@ def sojourn(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, s
     res = {"rc": rc, "steps": out, "stats": stats}
     res.update(stats_split(stats, net.n, R))
     return res
+
+
+def des_simulate(net: Network, dt: float, T: float, R: int, seed: int, rep_begin: int = 0,
+                 trace: bool = False):
+    """Exact event-by-event simulation (see exact_des.h) observed on the Euler
+    grid: dict with 'stats', its split views, 'events' and optionally 'N'
+    [K, n, R]."""
+    L = lib()
+    s, keep = _make_net(net)
+    n = net.n
+    K = num_steps(dt, T)
+    stats = np.zeros(6 * n + 4 * R, dtype=np.int64)
+    tr = np.zeros((K, n, R), dtype=np.int32) if trace else None
+    ev = np.zeros(1, dtype=np.int64)
+    rc = L.eo_des_simulate(C.byref(s), dt, T, R, seed, rep_begin, _ptr(stats), _ptr(tr), _ptr(ev))
+    del keep
+    if rc != 0:
+        raise RuntimeError(f"oracle eo_des_simulate failed with code {rc}")
+    out = {"stats": stats, "K": K, "events": int(ev[0])}
+    out.update(stats_split(stats, n, R))
+    if trace:
+        out["N"] = tr
+    return out
 
 
 def sojourn_pstay(x: int, d: int, m: int) -> float:

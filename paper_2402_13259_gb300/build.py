@@ -21,6 +21,9 @@ SOURCES = ["kernels.cu", "pipeline.cu", "abi.cu", "noalloc.cu", "batch.cu", "soj
 HEADERS = ["sampling.cuh", "internal.h", "handle.h", "unit.cuh", "tile.cuh", os.path.join("..", "..", "include", "eulernet.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")
+# extra nvcc arguments for tuning builds (e.g. "-DEN_HBM_MIN_BLOCKS=3"); the
+# objects are not rebuilt when only this changes, so pass --force with it
+EXTRA_FLAGS = os.environ.get("EULERNET_NVCC_EXTRA", "").split()
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + [
     "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
@@ -47,7 +50,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or _newer(o, [s] + headers):
             extra = ["-Xptxas", "-v"] if verbose else []
-            jobs.append([NVCC, *FLAGS, *extra, "-c", s, "-o", o])
+            jobs.append([NVCC, *FLAGS, *EXTRA_FLAGS, *extra, "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

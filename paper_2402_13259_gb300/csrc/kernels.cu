@@ -188,6 +188,9 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
 // ---- HBM-state form -------------------------------------------------------------
 
 constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
+#ifndef EN_HBM_MIN_BLOCKS
+#define EN_HBM_MIN_BLOCKS 4  // resident 256-thread CTAs per SM the register budget targets
+#endif
 
 // Units of one phase over stations lvl_station[s0 .. s0+m) (phases 2, 3) or
 // 0 .. m (phases 0, 1, 4), at device counter + koff.  Grid: x over
@@ -209,7 +212,7 @@ constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
 // station sums with one warp reduction and its per-replication sums with one
 // atomic per value, so a warp whose station drew cheap samples leaves at once.
 template <int PHASE, bool EXT = true>
-__global__ void __launch_bounds__(256, 4) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
+__global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
                                                            int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
   __shared__ float rinv_s[8 * 64];

@@ -30,6 +30,13 @@
 #define EN_HD inline
 #define EN_D inline
 #endif
+// The Philox block function is inlined at every draw site unless
+// EN_PHILOX_OUTLINE is defined (one out-of-line copy: smaller code).
+#if defined(__CUDACC__) && defined(EN_PHILOX_OUTLINE)
+#define EN_REFILL __device__ __noinline__
+#else
+#define EN_REFILL EN_D
+#endif
 
 namespace eulernet {
 
@@ -177,7 +184,7 @@ struct PhiloxStream {
     block = 0;
   }
 
-  EN_D void refill() {
+  EN_REFILL void refill() {
     uint32_t x0 = ctr0 | block, x1 = ctr1, x2 = ctr2, x3 = ctr3;
     uint32_t k0 = key0, k1 = key1;
 #pragma unroll

@@ -1,8 +1,9 @@
 """The pins of test_oracle_pins.py must reject plausible slips in the oracle.
 
-Each case plants one mistake in a copy of oracle/euler_oracle.c, builds it to
-a temporary library and runs the pin suite against it in a subprocess; the
-suite must fail.  Nothing here touches a GPU.
+Each case plants one mistake in a copy of oracle/euler_oracle.c (checked by
+test_oracle_pins.py) or oracle/exact_des.c (checked by test_oracle_des.py),
+builds the copy to a temporary library and runs that suite against it in a
+subprocess; the suite must fail.  Nothing here touches a GPU.
 """
 import os
 import shutil
@@ -13,7 +14,6 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "euler_oracle.c")
 
 MUTANTS = [
     # Algorithm 1, T > h branch: Binomial(x - m - 1, h/T) -> Binomial(x - m, h/T)
@@ -73,22 +73,38 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_reject_mutant(name, old, new):
-    src = open(SRC).read()
+# Slips in the exact DES, which test_oracle_des.py must reject.
+DES_MUTANTS = [
+    # thinning: every arrival candidate accepted (arrivals at the bound's rate)
+    ("des_no_thinning", "if (lmax[i] > 0.0 && rng_u01(&g) * lmax[i] < rate_at(net, i, t)) {",
+     "if (lmax[i] > 0.0) {"),
+    # service completions at rate N mu instead of min(N, m) mu
+    ("des_busy_uncapped", "const int64_t busy = N[i] < m[i] ? N[i] : m[i];", "const int64_t busy = N[i];"),
+    # routing ignores the probabilities: always the first edge
+    ("des_route_first_edge", "if (v < net->prob[e]) {", "if (v < 2.0) {"),
+]
+
+CASES = ([(n, "euler_oracle.c", o, w, "test_oracle_pins.py") for n, o, w in MUTANTS] +
+         [(n, "exact_des.c", o, w, "test_oracle_des.py") for n, o, w in DES_MUTANTS])
+
+
+@pytest.mark.parametrize("name,target,old,new,suite", CASES, ids=[c[0] for c in CASES])
+def test_pins_reject_mutant(name, target, old, new, suite):
+    src = open(os.path.join(ROOT, "oracle", target)).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not unique"
     tmp = tempfile.mkdtemp(prefix=f"mut_{name}_")
     try:
-        cfile = os.path.join(tmp, "euler_oracle.c")
-        with open(cfile, "w") as f:
+        for f in ("euler_oracle.c", "exact_des.c", "euler_oracle.h", "exact_des.h"):
+            shutil.copy(os.path.join(ROOT, "oracle", f), tmp)
+        with open(os.path.join(tmp, target), "w") as f:
             f.write(src.replace(old, new))
-        shutil.copy(os.path.join(ROOT, "oracle", "euler_oracle.h"), tmp)
         so = os.path.join(tmp, "liboracle.so")
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", so, cfile, "-lm"])
+                               "-fPIC", "-shared", "-o", so, os.path.join(tmp, "euler_oracle.c"),
+                               os.path.join(tmp, "exact_des.c"), "-lm"])
         env = dict(os.environ, EULER_ORACLE_SO=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                            os.path.join(ROOT, "tests", suite)],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
     finally:

@@ -14,7 +14,7 @@ a transposed routing index, a wrong arrival integral -- fails at least one:
 * the infinite-server closed form (Lemma 1(1) + Poisson thinning) of both
   schemes on a random DAG with time-varying arrivals;
 * the exact single-station distribution by brute-force convolution;
-* Argument 2 and Argument 3 (Sec. 4.1), Theorem 1's steady-state bracketing
+* Argument 2 and Argument 3 (Sec. 5.1), Theorem 1's steady-state bracketing
   of the Erlang-C mean and gap lambda*h, Theorem 2's per-node gap;
 * the arrival integral of Sec. 2.1.1 and the bookkeeping invariants;
 * the sojourn sampler of Sec. 6 (Algorithm 4): Lemma 3 against the exact
@@ -600,7 +600,7 @@ def test_average_scheme_second_order_on_infinite_server(orc):
 
 
 # ---------------------------------------------------------------------------
-# Simpler departure samplers, Eq. (1) and Eq. (2) of Sec. 3.1
+# Simpler departure samplers, Eq. (1) and Eq. (2) of Sec. 4.1.1 and 4.1.2
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("x,m,mu,h", [(4, 6, 1.0, 0.5), (12, 3, 2.0, 0.5), (30, 8, 0.5, 2.0)])
 def test_naive_departure_laws(orc, x, m, mu, h):
