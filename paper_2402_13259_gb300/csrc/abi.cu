@@ -344,7 +344,11 @@ int64_t hbm_slots(const euler_net* h, int32_t scheme, int64_t K) {
   return scheme == EULER_BACKWARD ? K + 1 : K + h->L - 1;
 }
 
-int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl, cudaStream_t s) {
+// The HBM form of one call: init, the graph of per-step kernels replayed to
+// the horizon, finish.  With grad, the kernels also sum the score terms into
+// mu_acc / th_acc (zeroed here) and the scores are written to p.scores.
+int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl, cudaStream_t s,
+            bool grad = false, double* mu_acc = nullptr, double* th_acc = nullptr) {
   int rc = ensure_hbm_state(h, p.R);
   if (rc) return rc;
   HbmState hs;
@@ -355,6 +359,12 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   hs.ld = h->hbm_cap_ld;
   hs.pos_level = h->d_pos_level;
   hs.depth = h->hbm_depth;
+  hs.mu_acc = mu_acc;
+  hs.th_acc = th_acc;
+  if (grad) {
+    CUDA_TRY(cudaMemsetAsync(mu_acc, 0, sizeof(double) * (size_t)h->n * hs.ld, s));
+    CUDA_TRY(cudaMemsetAsync(th_acc, 0, sizeof(double) * (size_t)std::max(h->n_ex, 1) * 3 * hs.ld, s));
+  }
   CUDA_TRY(launch_hbm_init(t, p, hs, s));
   // backward: K + 1 fused slots; forward: K + L - 1 skewed slots
   const int64_t slots = hbm_slots(h, p.scheme, p.K);
@@ -365,7 +375,7 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   cudaGraphExec_t exec = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   for (int64_t k = 0; k <= S; ++k) {
-    cudaError_t e = k < S ? launch_hbm_slot(t, p, hs, pl.block, (int32_t)k, h->cap_stream)
+    cudaError_t e = k < S ? launch_hbm_slot(t, p, hs, pl.block, (int32_t)k, grad, h->cap_stream)
                           : launch_hbm_advance(hs, (int32_t)S, h->cap_stream);
     if (e != cudaSuccess) {
       cudaStreamEndCapture(h->cap_stream, &graph);
@@ -382,6 +392,7 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   cudaGraphExecDestroy(exec);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   CUDA_TRY(launch_hbm_finish(t, p, hs, s));
+  if (grad) CUDA_TRY(launch_hbm_scores(t, p, hs, s));
   return EULER_OK;
 }
 
@@ -469,6 +480,8 @@ void euler_net_destroy(euler_net* h) {
   cudaFree(h->d_col);
   cudaFree(h->d_sstats);
   cudaFree(h->d_pos_level);
+  cudaFree(h->d_gmu);
+  cudaFree(h->d_gth);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -784,6 +797,49 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
   const int64_t nb = (R + 31) / 32;
   rc = grow(&h->d_gpartial, &h->gpartial_cap, (size_t)(4 * nb * C + 2 * nb));
   if (rc) return rc;
+  // At scale the HBM form (score sums per station and replication in global
+  // memory, the same step order) is faster, as for euler_net_simulate.
+  const int forced = (int)h->opt[EULER_OPT_FORM];
+  if (forced == 2 || (forced <= 0 && (int64_t)h->n * R >= kHbmMinUnitsPerStep)) {
+    const int64_t ld = (R + 3) / 4 * 4;
+    rc = grow(&h->d_gmu, &h->gmu_cap, (size_t)(h->n * ld));
+    if (rc) return rc;
+    rc = grow(&h->d_gth, &h->gth_cap, (size_t)(std::max(h->n_ex, 1) * 3 * ld));
+    if (rc) return rc;
+    RunParams p;
+    std::memset(&p, 0, sizeof p);
+    p.p0 = h->d_p0;
+    p.lam = h->d_lam;
+    p.h = (float)dt;
+    p.K = (int32_t)K;
+    p.key0 = (uint32_t)seed;
+    p.key1 = (uint32_t)(seed >> 32);
+    p.R = R;
+    p.rep_begin = rep_begin;
+    p.scheme = scheme;
+    p.tile_reps = 32;
+    p.num_tiles = (R + 31) / 32;
+    p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+    p.stats = stats;
+    p.err = h->d_err;
+    p.wait_limit = (int64_t)1 << 25;
+    p.p0f = h->d_p0f;
+    p.dlam = h->d_dlam;
+    p.scores = scores;
+    p.muh = h->d_muh;
+    p.dep_mode = 0;
+    p.mtab = h->mtab();
+    Plan pl;
+    pl.form = 2;
+    pl.block = h->opt[EULER_OPT_BLOCK] > 0 ? (int)h->opt[EULER_OPT_BLOCK] : kHbmBlock;
+    if (pl.block % 32 || pl.block > 256) return fail(EULER_ERR_ARG, "HBM-form block must be a multiple of 32 <= 256");
+    CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s));
+    rc = run_hbm(h, h->tables(), p, pl, s, true, h->d_gmu, h->d_gth);
+    if (rc) return rc;
+    cudaError_t e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
+    return EULER_OK;
+  }
   // tile: the largest power of two <= 32 whose state and score sums fit
   int Rt = 32;
   int64_t smem = 0;

@@ -52,6 +52,10 @@ struct euler_net {
   size_t gscores_cap = 0;
   double* d_gpartial = nullptr;
   size_t gpartial_cap = 0;
+  double* d_gmu = nullptr;  // HBM-form gradients: score sums [n][ld]
+  size_t gmu_cap = 0;
+  double* d_gth = nullptr;  // and [n_ex][3][ld]
+  size_t gth_cap = 0;
 
   // scratch of the average scheme
   int64_t* d_avg_b = nullptr;

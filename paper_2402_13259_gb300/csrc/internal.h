@@ -110,6 +110,8 @@ struct HbmState {
   int64_t ld;      // leading dimension (>= R, multiple of 4)
   const int32_t* pos_level = nullptr;  // [n] level of lvl_station[k] (skewed forward only)
   int32_t depth = 1;                   // ring slots of Redge: max level gap of an edge + 1
+  double* mu_acc = nullptr;            // gradients: [n][ld] score sums in mu_i, step order
+  double* th_acc = nullptr;            // gradients: [n_ex][3][ld] score sums in (a, b, phase)
 };
 int64_t hbm_smem_bytes(int32_t n, int32_t tile_reps);
 cudaError_t launch_hbm_init(const NetTables& t, const RunParams& p, const HbmState& hs,
@@ -123,7 +125,10 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
 // forward, skewed slot tau (every station i runs its step tau - level(i) when
 // that lies in 1..K).  Does not advance the counter.
 cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
-                            int32_t koff, cudaStream_t s);
+                            int32_t koff, bool grad, cudaStream_t s);
+// Gradients in the HBM form: p.scores[r][c] from the score sums of hs.
+cudaError_t launch_hbm_scores(const NetTables& t, const RunParams& p, const HbmState& hs,
+                              cudaStream_t s);
 cudaError_t launch_hbm_advance(const HbmState& hs, int32_t by, cudaStream_t s);
 cudaError_t launch_hbm_finish(const NetTables& t, const RunParams& p, const HbmState& hs,
                               cudaStream_t s);

@@ -211,7 +211,23 @@ constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
 // Warps never wait for one another: each keeps its own 1/k table, adds its
 // station sums with one warp reduction and its per-replication sums with one
 // atomic per value, so a warp whose station drew cheap samples leaves at once.
-template <int PHASE, bool EXT = true>
+// Score terms of one unit into the HBM form's per-(station, replication)
+// sums: each cell belongs to one lane, so the float64 sums run in step order.
+__device__ __forceinline__ void hbm_add_scores(const NetTables& t, const RunParams& p,
+                                               const HbmState& hs, int32_t i, int32_t tau,
+                                               int64_t rloc, const UnitOut& o) {
+  hs.mu_acc[(int64_t)i * hs.ld + rloc] += (double)o.smu;
+  if (!isnan(o.garr)) {
+    const int32_t ec = __ldg(t.ex_col + i);
+    const float* dl = p.dlam + ((int64_t)(tau - 1) * t.n_ex + ec) * 3;
+    double* th = hs.th_acc + (int64_t)ec * 3 * hs.ld + rloc;
+    th[0] += (double)(o.garr * __ldg(dl + 0));
+    th[hs.ld] += (double)(o.garr * __ldg(dl + 1));
+    th[2 * hs.ld] += (double)(o.garr * __ldg(dl + 2));
+  }
+}
+
+template <int PHASE, bool EXT = true, bool GRAD = false>
 __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
                                                            int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
@@ -274,7 +290,8 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
         }
         if (slot <= p.K) {
           int32_t* rcur = hs.Redge + (int64_t)(slot & 1) * t.E * hs.ld;
-          const UnitOut o = unit_update<false, false, EXT>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx);
+          const UnitOut o = unit_update<false, GRAD, EXT>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx);
+          if (GRAD) hbm_add_scores(t, p, hs, i, slot, rloc, o);
           v[2] = o.D; v[3] = o.X; v[4] = o.A;
           part[1] += o.D; part[2] += o.X; part[3] += o.A;
         }
@@ -283,7 +300,8 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
     } else {  // forward: one level (2) or a skewed slot (3)
       int32_t v[5] = {0, 0, 0, 0, 0};
       if (act) {
-        const UnitOut o = unit_update<true, false, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
+        const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
+        if (GRAD) hbm_add_scores(t, p, hs, i, tau, rloc, o);
         const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
         v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
         part[0] += o.N; part[1] += o.D; part[2] += o.X; part[3] += o.A;
@@ -480,23 +498,57 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
   return cudaGetLastError();
 }
 
+namespace {
+template <bool GRAD>
+void launch_slot_kernel(const NetTables& t, const RunParams& p, const HbmState& hs, dim3 grid,
+                        int block, int32_t koff, bool ext, cudaStream_t s) {
+  if (p.scheme == 0) {
+    if (ext)
+      hbm_phase_kernel<4, true, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+    else
+      hbm_phase_kernel<4, false, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+  } else {
+    if (ext)
+      hbm_phase_kernel<3, true, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+    else
+      hbm_phase_kernel<3, false, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+  }
+}
+
+// S_r: mu_i sums, then (a, b, phase) summed over external stations in order.
+__global__ void hbm_scores_kernel(NetTables t, RunParams p, HbmState hs) {
+  const int64_t C = (int64_t)t.n + 3;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.R * C;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = k / C, c = k % C;
+    double v;
+    if (c < t.n) {
+      v = hs.mu_acc[c * hs.ld + r];
+    } else {
+      v = 0.0;
+      for (int32_t ec = 0; ec < t.n_ex; ++ec) v += hs.th_acc[((int64_t)ec * 3 + (c - t.n)) * hs.ld + r];
+    }
+    p.scores[k] = v;
+  }
+}
+}  // namespace
+
 cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
-                            int32_t koff, cudaStream_t s) {
+                            int32_t koff, bool grad, cudaStream_t s) {
   const int G = block / kHbmTile;  // stations per block
   const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
   dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
   const bool ext = p.mtab != nullptr || p.dep_mode != 0;
-  if (p.scheme == 0) {
-    if (ext)
-      hbm_phase_kernel<4, true><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-    else
-      hbm_phase_kernel<4, false><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-  } else {
-    if (ext)
-      hbm_phase_kernel<3, true><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-    else
-      hbm_phase_kernel<3, false><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-  }
+  if (grad)
+    launch_slot_kernel<true>(t, p, hs, grid, block, koff, ext, s);
+  else
+    launch_slot_kernel<false>(t, p, hs, grid, block, koff, ext, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_scores(const NetTables& t, const RunParams& p, const HbmState& hs,
+                              cudaStream_t s) {
+  hbm_scores_kernel<<<1024, 256, 0, s>>>(t, p, hs);
   return cudaGetLastError();
 }
 

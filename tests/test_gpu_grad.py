@@ -35,12 +35,16 @@ def _cases():
     return [(_queueing_net(), 0.3, 3.0, 300), (W.tandem3().net, 0.01, 2.0, 100), (dag, 0.05, 2.5, 70)]
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("case", range(3))
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_grad_matches_oracle_exactly(Bd, orc, case, scheme):
+def test_grad_matches_oracle_exactly(Bd, orc, case, scheme, form):
+    """Persistent form (score sums in shared memory) and HBM form (score sums
+    per station and replication in global memory) both match the oracle."""
     net, dt, T, R = _cases()[case]
     h = Bd.EulerNet(net)
     try:
+        h.set_option(Bd.OPT_FORM, form)
         g = h.grad(scheme, dt, T, R, 31, rep_begin=5, scores=True, stats=True)
     finally:
         h.close()
@@ -55,8 +59,9 @@ def test_grad_matches_oracle_exactly(Bd, orc, case, scheme):
 
 def test_grad_full_size_sampled_scores(Bd, orc):
     """The differentiation workload at full size (100-station DAG, sinusoid
-    theta = (1, 0.3, 0), 100,000 replications, T = 100, dt = 0.01): sampled
-    replications' scores re-run by the oracle match bit for bit."""
+    theta = (1, 0.3, 0), 100,000 replications, T = 100, dt = 0.01; the
+    planner's form): sampled replications' scores re-run by the oracle match
+    bit for bit."""
     run = W.sinusoid_dag()
     h = Bd.EulerNet(run.net)
     try:
