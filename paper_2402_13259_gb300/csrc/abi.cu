@@ -199,10 +199,6 @@ bool make_pipe_plan(const euler_net* h, int W, PipePlan* pp) {
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// Units per step (n R) from which the planner takes the HBM form, and its
-// default threads per block.
-constexpr int64_t kHbmMinUnitsPerStep = int64_t(1) << 18;
-constexpr int kHbmBlock = 256;
 
 int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   const int64_t limit = h->smem_optin;
@@ -344,11 +340,15 @@ int64_t hbm_slots(const euler_net* h, int32_t scheme, int64_t K) {
   return scheme == EULER_BACKWARD ? K + 1 : K + h->L - 1;
 }
 
+}  // namespace
+
 // The HBM form of one call: init, the graph of per-step kernels replayed to
-// the horizon, finish.  With grad, the kernels also sum the score terms into
-// mu_acc / th_acc (zeroed here) and the scores are written to p.scores.
-int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl, cudaStream_t s,
-            bool grad = false, double* mu_acc = nullptr, double* th_acc = nullptr) {
+// the horizon, finish.  Gradients: the kernels also sum the score terms into
+// x.mu_acc / x.th_acc (zeroed here) and the scores go to p.scores.  Sojourn
+// times: the customers start at x.station, step x.tau0, and their sojourns go
+// to x.out.
+int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p, int block,
+                           cudaStream_t s, const HbmExtra& x) {
   int rc = ensure_hbm_state(h, p.R);
   if (rc) return rc;
   HbmState hs;
@@ -359,12 +359,18 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   hs.ld = h->hbm_cap_ld;
   hs.pos_level = h->d_pos_level;
   hs.depth = h->hbm_depth;
-  hs.mu_acc = mu_acc;
-  hs.th_acc = th_acc;
-  if (grad) {
-    CUDA_TRY(cudaMemsetAsync(mu_acc, 0, sizeof(double) * (size_t)h->n * hs.ld, s));
-    CUDA_TRY(cudaMemsetAsync(th_acc, 0, sizeof(double) * (size_t)std::max(h->n_ex, 1) * 3 * hs.ld, s));
+  hs.mu_acc = x.mu_acc;
+  hs.th_acc = x.th_acc;
+  hs.cloc = x.cloc;
+  hs.cpos = x.cpos;
+  hs.csteps = x.csteps;
+  hs.col = x.col;
+  hs.S = x.S;
+  if (x.mode == kHbmGrad) {
+    CUDA_TRY(cudaMemsetAsync(x.mu_acc, 0, sizeof(double) * (size_t)h->n * hs.ld, s));
+    CUDA_TRY(cudaMemsetAsync(x.th_acc, 0, sizeof(double) * (size_t)std::max(h->n_ex, 1) * 3 * hs.ld, s));
   }
+  if (x.mode == kHbmSojourn) CUDA_TRY(launch_hbm_sojourn_init(p, hs, x.station, x.tau0, s));
   CUDA_TRY(launch_hbm_init(t, p, hs, s));
   // backward: K + 1 fused slots; forward: K + L - 1 skewed slots
   const int64_t slots = hbm_slots(h, p.scheme, p.K);
@@ -375,7 +381,7 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   cudaGraphExec_t exec = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   for (int64_t k = 0; k <= S; ++k) {
-    cudaError_t e = k < S ? launch_hbm_slot(t, p, hs, pl.block, (int32_t)k, grad, h->cap_stream)
+    cudaError_t e = k < S ? launch_hbm_slot(t, p, hs, block, (int32_t)k, x.mode, h->cap_stream)
                           : launch_hbm_advance(hs, (int32_t)S, h->cap_stream);
     if (e != cudaSuccess) {
       cudaStreamEndCapture(h->cap_stream, &graph);
@@ -392,9 +398,12 @@ int run_hbm(euler_net* h, const NetTables& t, const RunParams& p, const Plan& pl
   cudaGraphExecDestroy(exec);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   CUDA_TRY(launch_hbm_finish(t, p, hs, s));
-  if (grad) CUDA_TRY(launch_hbm_scores(t, p, hs, s));
+  if (x.mode == kHbmGrad) CUDA_TRY(launch_hbm_scores(t, p, hs, s));
+  if (x.mode == kHbmSojourn) CUDA_TRY(launch_hbm_sojourn_finish(p, hs, x.out, s));
   return EULER_OK;
 }
+
+namespace {
 
 int validate_net(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* prob,
                  const int32_t* servers, const double* mu, const euler_arrivals* arr,
@@ -482,6 +491,9 @@ void euler_net_destroy(euler_net* h) {
   cudaFree(h->d_pos_level);
   cudaFree(h->d_gmu);
   cudaFree(h->d_gth);
+  cudaFree(h->d_cloc);
+  cudaFree(h->d_cpos);
+  cudaFree(h->d_csteps);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -703,7 +715,7 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
     if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
     return EULER_OK;
   }
-  return run_hbm(h, t, p, pl, s);
+  return run_hbm_form(h, t, p, pl.block, s, HbmExtra());
 }
 
 }  // extern "C"
@@ -834,7 +846,11 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
     pl.block = h->opt[EULER_OPT_BLOCK] > 0 ? (int)h->opt[EULER_OPT_BLOCK] : kHbmBlock;
     if (pl.block % 32 || pl.block > 256) return fail(EULER_ERR_ARG, "HBM-form block must be a multiple of 32 <= 256");
     CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s));
-    rc = run_hbm(h, h->tables(), p, pl, s, true, h->d_gmu, h->d_gth);
+    HbmExtra xg;
+    xg.mode = kHbmGrad;
+    xg.mu_acc = h->d_gmu;
+    xg.th_acc = h->d_gth;
+    rc = run_hbm_form(h, h->tables(), p, pl.block, s, xg);
     if (rc) return rc;
     cudaError_t e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var, s);
     if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");

@@ -56,6 +56,10 @@ struct euler_net {
   size_t gmu_cap = 0;
   double* d_gth = nullptr;  // and [n_ex][3][ld]
   size_t gth_cap = 0;
+  unsigned long long* d_cloc = nullptr;  // HBM-form sojourn times: customer state
+  int32_t* d_cpos = nullptr;
+  int32_t* d_csteps = nullptr;
+  size_t cust_cap = 0;
 
   // scratch of the average scheme
   int64_t* d_avg_b = nullptr;
@@ -101,6 +105,29 @@ struct euler_net {
 };
 
 namespace eulernet {
+// Units per step (n R) from which the planner takes the HBM form, and its
+// default threads per block.
+constexpr int64_t kHbmMinUnitsPerStep = int64_t(1) << 18;
+constexpr int kHbmBlock = 256;
+
+// What an HBM-form run computes besides the statistics (see HbmMode).
+struct HbmExtra {
+  int mode = kHbmPlain;
+  double* mu_acc = nullptr;            // gradients: score sums, zeroed by the run
+  double* th_acc = nullptr;
+  unsigned long long* cloc = nullptr;  // sojourn times: customer state [S][ld]
+  int32_t* cpos = nullptr;
+  int32_t* csteps = nullptr;
+  const int32_t* col = nullptr;
+  int32_t S = 0, station = 0, tau0 = 0;
+  int32_t* out = nullptr;              // [R][S]
+};
+
+// One call in the HBM form: state set-up, the graph of per-step kernels
+// replayed to the horizon, statistics (and scores / sojourn times) out.
+int run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p, int block, cudaStream_t s,
+                 const HbmExtra& x);
+
 // Per-step mean of the external arrivals of station i over step tau: the
 // exact integral of lambda_i over ((tau-1) dt, tau dt] (Sec. 2.1.1), in double.
 double step_mean(const euler_net& h, int32_t i, int64_t tau, double dt);

@@ -112,7 +112,16 @@ struct HbmState {
   int32_t depth = 1;                   // ring slots of Redge: max level gap of an edge + 1
   double* mu_acc = nullptr;            // gradients: [n][ld] score sums in mu_i, step order
   double* th_acc = nullptr;            // gradients: [n_ex][3][ld] score sums in (a, b, phase)
+  // sojourn times (Algorithm 4): tagged customers c < S of every replication
+  unsigned long long* cloc = nullptr;  // [S][ld] station << 32 | due step << 1 | setup pending
+  int32_t* cpos = nullptr;             // [S][ld] > 0 waiting position, 0 in service
+  int32_t* csteps = nullptr;           // [S][ld] steps accounted
+  const int32_t* col = nullptr;        // [E] destination station of each edge
+  int32_t S = 0;
 };
+
+// What the HBM form's per-step kernels compute besides the step.
+enum HbmMode { kHbmPlain = 0, kHbmGrad = 1, kHbmSojourn = 2 };
 int64_t hbm_smem_bytes(int32_t n, int32_t tile_reps);
 cudaError_t launch_hbm_init(const NetTables& t, const RunParams& p, const HbmState& hs,
                             cudaStream_t s);
@@ -125,7 +134,13 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
 // forward, skewed slot tau (every station i runs its step tau - level(i) when
 // that lies in 1..K).  Does not advance the counter.
 cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
-                            int32_t koff, bool grad, cudaStream_t s);
+                            int32_t koff, int mode, cudaStream_t s);
+// Sojourn times in the HBM form: customers enter `station` in step tau0
+// (setup pending); finish writes out[r][c] (steps, or minus them if censored).
+cudaError_t launch_hbm_sojourn_init(const RunParams& p, const HbmState& hs, int32_t station,
+                                    int32_t tau0, cudaStream_t s);
+cudaError_t launch_hbm_sojourn_finish(const RunParams& p, const HbmState& hs, int32_t* out,
+                                      cudaStream_t s);
 // Gradients in the HBM form: p.scores[r][c] from the score sums of hs.
 cudaError_t launch_hbm_scores(const NetTables& t, const RunParams& p, const HbmState& hs,
                               cudaStream_t s);

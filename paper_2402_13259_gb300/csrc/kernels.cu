@@ -227,7 +227,95 @@ __device__ __forceinline__ void hbm_add_scores(const NetTables& t, const RunPara
   }
 }
 
-template <int PHASE, bool EXT = true, bool GRAD = false>
+// ---- sojourn times in the HBM form (Sec. 6, Algorithm 4, Lemma 3) ----------
+//
+// Tagged customer c of replication r has a packed word station << 32 | due
+// step << 1 | setup pending, a place (> 0 waiting, 0 in service) and a step
+// count.  The warp of the customer's station acts on it when it processes the
+// due step: a setup reads N of that step (the place is max(N, 1), waiting if
+// above m); a waiting step subtracts the step's departures; a service step
+// keeps the customer with Lemma 3's probability given the step's departure
+// input x and departures d, else sends it along the step's routed counts to
+// the next station (setup pending there for the same step) or out.  Another
+// station's warp may read the word while it is rewritten in the same launch:
+// it then sees either a different station or a due step it is not
+// processing, so the 64-bit word is read and written whole.
+constexpr unsigned long long kSojDone = 0xFFFFFFFFull << 32;
+
+__device__ __forceinline__ unsigned long long soj_pack(int32_t station, int32_t due, bool setup) {
+  return ((unsigned long long)(uint32_t)station << 32) | ((unsigned long long)(uint32_t)due << 1) |
+         (setup ? 1ull : 0ull);
+}
+
+// b^k (k >= 0) by binary powering, multiplications in a fixed order.
+__device__ __forceinline__ float soj_pow_int(float b, int32_t k) {
+  float r = 1.0f;
+  while (k > 0) {
+    if (k & 1) r = r * b;
+    b = b * b;
+    k >>= 1;
+  }
+  return r;
+}
+
+// Lemma 3: P(the tagged customer's service continues through the step | the
+// step's departure draw had input x and output d > 0, m servers).
+__device__ __forceinline__ float soj_stay(int32_t x, int32_t d, int32_t m) {
+  if (x <= m) return (float)(x - d) / (float)x;
+  const float q = (float)(m - 1) / (float)m;
+  if (x <= m + d) return soj_pow_int(q, x - m) * ((float)(x - d) / (float)m);
+  return soj_pow_int(q, d);
+}
+
+// Setup of customer word *lp at station i after step tau (N = N_tau,i).
+template <bool EXT>
+__device__ __forceinline__ void soj_setup(const NetTables& t, const RunParams& p, const HbmState& hs,
+                                          int64_t ci, int32_t i, int32_t tau, int32_t N) {
+  const int32_t pos = N < 1 ? 1 : N;
+  hs.cpos[ci] = pos > servers_at<EXT>(t, p, i, (uint32_t)tau) ? pos : 0;
+  hs.cloc[ci] = soj_pack(i, tau + 1, false);
+}
+
+// Waiting or service step tau of customer ci at station i (x, d: the step's
+// departure input and output; redge: its routed counts).
+template <bool EXT>
+__device__ __forceinline__ void soj_step(const NetTables& t, const RunParams& p, const HbmState& hs,
+                                         int64_t ci, int32_t c, int32_t i, int32_t tau, uint32_t rep,
+                                         int32_t x, int32_t d, const int32_t* redge, int64_t rloc) {
+  hs.csteps[ci] += 1;
+  const int32_t m = servers_at<EXT>(t, p, i, (uint32_t)tau);
+  int32_t pos = hs.cpos[ci];
+  if (pos > 0) {  // waiting step
+    pos -= d;
+    hs.cpos[ci] = pos <= m ? 0 : pos;
+    hs.cloc[ci] = soj_pack(i, tau + 1, false);
+    return;
+  }
+  if (d > 0) {
+    const float ps = soj_stay(x, d, m);
+    PhiloxStream cs;
+    cs.init(p.key0, p.key1, 3u, (uint32_t)c, (uint32_t)tau, rep);
+    const float u = cs.uniform();
+    const uint32_t w = cs.next();
+    if (!(u < ps)) {
+      uint32_t pick = __umulhi(w, (uint32_t)d);
+      const int32_t e1 = __ldg(t.row_ptr + i + 1);
+      for (int32_t e = __ldg(t.row_ptr + i); e < e1; ++e) {
+        const uint32_t v = (uint32_t)redge[(int64_t)e * hs.ld + rloc];
+        if (pick < v) {
+          hs.cloc[ci] = soj_pack(__ldg(hs.col + e), tau, true);
+          return;
+        }
+        pick -= v;
+      }
+      hs.cloc[ci] = kSojDone;
+      return;
+    }
+  }
+  hs.cloc[ci] = soj_pack(i, tau + 1, false);  // still in service
+}
+
+template <int PHASE, bool EXT = true, bool GRAD = false, bool SOJ = false>
 __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
                                                            int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
@@ -294,6 +382,28 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
           if (GRAD) hbm_add_scores(t, p, hs, i, slot, rloc, o);
           v[2] = o.D; v[3] = o.X; v[4] = o.A;
           part[1] += o.D; part[2] += o.X; part[3] += o.A;
+          if (SOJ) {
+            // customers due here: setups of step slot-1 (N = v[0]), then the
+            // waiting / service step slot (x = N_{slot-1}, d = D)
+            for (int32_t c = 0; c < hs.S; ++c) {
+              const int64_t ci = (int64_t)c * hs.ld + rloc;
+              unsigned long long w = hs.cloc[ci];
+              if ((uint32_t)(w >> 32) != (uint32_t)i) continue;
+              if ((w & 1ull) && (int32_t)((uint32_t)w >> 1) == slot - 1) {
+                soj_setup<EXT>(t, p, hs, ci, i, slot - 1, v[0]);
+                w = hs.cloc[ci];
+              }
+              if (!(w & 1ull) && (int32_t)((uint32_t)w >> 1) == slot)
+                soj_step<EXT>(t, p, hs, ci, c, i, slot, rep, o.x, o.D, rcur, rloc);
+            }
+          }
+        } else if (SOJ && slot >= 2) {  // slot K+1: the last setups only
+          for (int32_t c = 0; c < hs.S; ++c) {
+            const int64_t ci = (int64_t)c * hs.ld + rloc;
+            const unsigned long long w = hs.cloc[ci];
+            if ((uint32_t)(w >> 32) == (uint32_t)i && (w & 1ull) && (int32_t)((uint32_t)w >> 1) == slot - 1)
+              soj_setup<EXT>(t, p, hs, ci, i, slot - 1, v[0]);
+          }
         }
       }
       reduce_to<5>(st, v, lead, 32, true);
@@ -302,6 +412,17 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
       if (act) {
         const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
         if (GRAD) hbm_add_scores(t, p, hs, i, tau, rloc, o);
+        if (SOJ) {  // customers due here at step tau: a waiting / service step, or a setup
+          for (int32_t c = 0; c < hs.S; ++c) {
+            const int64_t ci = (int64_t)c * hs.ld + rloc;
+            const unsigned long long w = hs.cloc[ci];
+            if ((uint32_t)(w >> 32) != (uint32_t)i || (int32_t)((uint32_t)w >> 1) != tau) continue;
+            if (w & 1ull)
+              soj_setup<EXT>(t, p, hs, ci, i, tau, o.N);
+            else
+              soj_step<EXT>(t, p, hs, ci, c, i, tau, rep, o.x, o.D, redge, rloc);
+          }
+        }
         const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
         v[0] = o.N; v[1] = o.N < c ? o.N : c; v[2] = o.D; v[3] = o.X; v[4] = o.A;
         part[0] += o.N; part[1] += o.D; part[2] += o.X; part[3] += o.A;
@@ -499,19 +620,39 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
 }
 
 namespace {
-template <bool GRAD>
+template <bool GRAD, bool SOJ>
 void launch_slot_kernel(const NetTables& t, const RunParams& p, const HbmState& hs, dim3 grid,
                         int block, int32_t koff, bool ext, cudaStream_t s) {
   if (p.scheme == 0) {
     if (ext)
-      hbm_phase_kernel<4, true, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+      hbm_phase_kernel<4, true, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
     else
-      hbm_phase_kernel<4, false, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+      hbm_phase_kernel<4, false, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
   } else {
     if (ext)
-      hbm_phase_kernel<3, true, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+      hbm_phase_kernel<3, true, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
     else
-      hbm_phase_kernel<3, false, GRAD><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+      hbm_phase_kernel<3, false, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
+  }
+}
+
+__global__ void hbm_sojourn_init_kernel(RunParams p, HbmState hs, int32_t station, int32_t tau0) {
+  const int64_t total = (int64_t)hs.S * hs.ld;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    hs.cloc[k] = soj_pack(station, tau0, true);
+    hs.cpos[k] = 0;
+    hs.csteps[k] = 0;
+  }
+}
+
+__global__ void hbm_sojourn_finish_kernel(RunParams p, HbmState hs, int32_t* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.R * hs.S;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = k / hs.S, c = k % hs.S;
+    const int64_t ci = c * hs.ld + r;
+    const int32_t st = hs.csteps[ci];
+    out[k] = hs.cloc[ci] == kSojDone ? st : -st;
   }
 }
 
@@ -534,15 +675,29 @@ __global__ void hbm_scores_kernel(NetTables t, RunParams p, HbmState hs) {
 }  // namespace
 
 cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmState& hs, int block,
-                            int32_t koff, bool grad, cudaStream_t s) {
+                            int32_t koff, int mode, cudaStream_t s) {
   const int G = block / kHbmTile;  // stations per block
   const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
   dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
   const bool ext = p.mtab != nullptr || p.dep_mode != 0;
-  if (grad)
-    launch_slot_kernel<true>(t, p, hs, grid, block, koff, ext, s);
+  if (mode == kHbmGrad)
+    launch_slot_kernel<true, false>(t, p, hs, grid, block, koff, ext, s);
+  else if (mode == kHbmSojourn)
+    launch_slot_kernel<false, true>(t, p, hs, grid, block, koff, ext, s);
   else
-    launch_slot_kernel<false>(t, p, hs, grid, block, koff, ext, s);
+    launch_slot_kernel<false, false>(t, p, hs, grid, block, koff, ext, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_sojourn_init(const RunParams& p, const HbmState& hs, int32_t station,
+                                    int32_t tau0, cudaStream_t s) {
+  hbm_sojourn_init_kernel<<<512, 256, 0, s>>>(p, hs, station, tau0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hbm_sojourn_finish(const RunParams& p, const HbmState& hs, int32_t* out,
+                                      cudaStream_t s) {
+  hbm_sojourn_finish_kernel<<<512, 256, 0, s>>>(p, hs, out);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
 // sojourn.cu -- euler_net_sojourn: sojourn times of tagged customers (Sec. 6,
 // Algorithm 4, with the conditional stay probability of Lemma 3), sampled
-// while the Euler time loop runs.
+// while the Euler time loop runs.  This file holds the persistent
+// shared-memory form; at scale the HBM form's per-step kernels (kernels.cu)
+// advance the customers instead, with the same results.
 //
 // Algorithm 4 reads, for each step after the customer's entry, the values
 // that step produced at the customer's station: the departure draw's input x
@@ -260,6 +262,59 @@ extern "C" int euler_net_sojourn(euler_net* h, int32_t scheme, double dt, double
   e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * len, s);
   if (e != cudaSuccess) return cuda_fail(e, "statistics clear");
   if (R == 0) return EULER_OK;
+  RunParams p;
+  std::memset(&p, 0, sizeof p);
+  p.p0 = h->d_p0;
+  p.lam = h->d_lam;
+  p.h = (float)dt;
+  p.K = (int32_t)K;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.R = R;
+  p.rep_begin = rep_begin;
+  p.scheme = scheme;
+  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+  p.stats = stats;
+  p.err = h->d_err;
+  p.wait_limit = (int64_t)1 << 25;
+  p.muh = h->d_muh;
+  p.dep_mode = h->dep_mode();
+  p.mtab = h->mtab();
+  // At scale the HBM form, as for euler_net_simulate: the customers' state
+  // lives in global memory and the warp of a customer's station advances it.
+  const int forced = (int)h->opt[EULER_OPT_FORM];
+  if (forced == 2 || (forced <= 0 && (int64_t)h->n * R >= kHbmMinUnitsPerStep)) {
+    const int64_t ld = (R + 3) / 4 * 4;
+    const size_t need = (size_t)samples * (size_t)ld;
+    if (need > h->cust_cap) {
+      cudaFree(h->d_cloc);
+      cudaFree(h->d_cpos);
+      cudaFree(h->d_csteps);
+      h->d_cloc = nullptr;
+      h->d_cpos = h->d_csteps = nullptr;
+      h->cust_cap = 0;
+      e = cudaMalloc(&h->d_cloc, sizeof(unsigned long long) * need);
+      if (e == cudaSuccess) e = cudaMalloc(&h->d_cpos, sizeof(int32_t) * need);
+      if (e == cudaSuccess) e = cudaMalloc(&h->d_csteps, sizeof(int32_t) * need);
+      if (e != cudaSuccess) return cuda_fail(e, "sojourn customer state");
+      h->cust_cap = need;
+    }
+    const int block = h->opt[EULER_OPT_BLOCK] > 0 ? (int)h->opt[EULER_OPT_BLOCK] : kHbmBlock;
+    if (block % 32 || block > 256) return fail(EULER_ERR_ARG, "HBM-form block must be a multiple of 32 <= 256");
+    p.tile_reps = 32;
+    p.num_tiles = (R + 31) / 32;
+    HbmExtra x;
+    x.mode = kHbmSojourn;
+    x.cloc = h->d_cloc;
+    x.cpos = h->d_cpos;
+    x.csteps = h->d_csteps;
+    x.col = h->d_col;
+    x.S = samples;
+    x.station = station;
+    x.tau0 = (int32_t)tau0;
+    x.out = sojourn;
+    return run_hbm_form(h, h->tables(), p, block, s, x);
+  }
   // tile: the largest power of two <= 32 whose state and customers fit
   int Rt = 32;
   int64_t smem = 0;
@@ -276,26 +331,8 @@ extern "C" int euler_net_sojourn(euler_net* h, int32_t scheme, double dt, double
   G = (G + quantum - 1) / quantum * quantum;
   if (G * Rt > 512) G = 512 / Rt;
   const int block = (int)std::max<int64_t>(G * Rt, 32);
-  RunParams p;
-  std::memset(&p, 0, sizeof p);
-  p.p0 = h->d_p0;
-  p.lam = h->d_lam;
-  p.h = (float)dt;
-  p.K = (int32_t)K;
-  p.key0 = (uint32_t)seed;
-  p.key1 = (uint32_t)(seed >> 32);
-  p.R = R;
-  p.rep_begin = rep_begin;
-  p.scheme = scheme;
   p.tile_reps = Rt;
   p.num_tiles = (R + Rt - 1) / Rt;
-  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
-  p.stats = stats;
-  p.err = h->d_err;
-  p.wait_limit = (int64_t)1 << 25;
-  p.muh = h->d_muh;
-  p.dep_mode = h->dep_mode();
-  p.mtab = h->mtab();
   SojournParams q;
   q.col = h->d_col;
   q.out = sojourn;

@@ -54,64 +54,74 @@ def _check(Bd, orc, net, scheme, dt, T, R, seed, station, tau0, samples, rep_beg
     return got
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_tandem_sojourn_parity(Bd, orc, scheme):
+def test_tandem_sojourn_parity(Bd, orc, scheme, form):
     """3-station tandem, 200 replications (6 full tiles and a ragged one), 3
-    tagged customers each, entering mid-run."""
+    tagged customers each, entering mid-run; the persistent form (customers in
+    shared memory) and the HBM form (customers in global memory)."""
     run = W.tandem3()
-    got = _check(Bd, orc, run.net, scheme, run.dt, 6.0, 200, run.seed, 0, 100, 3)
+    got = _check(Bd, orc, run.net, scheme, run.dt, 6.0, 200, run.seed, 0, 100, 3,
+                 options={Bd.OPT_FORM: form})
     assert (got > 0).mean() > 0.5
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("seed", [3, 8])
-def test_random_dag_sojourn_parity(Bd, orc, scheme, seed):
+def test_random_dag_sojourn_parity(Bd, orc, scheme, seed, form):
     """Random small DAGs (skips across layers, several out-edges, queues that
-    build and drain), several entry stations and steps, a replication offset."""
+    build and drain), several entry stations and steps, a replication offset;
+    both forms."""
     rng = np.random.default_rng(seed)
     net = W.random_small_dag(rng, 9, max_deg=3, m_range=(1, 6), ext_frac=0.5, lam_scale=6.0)
     net.N0 = rng.integers(0, 12, size=net.n).astype(np.int32)
     for station, tau0 in [(0, 1), (int(rng.integers(0, net.n)), 37), (net.n - 1, 150)]:
-        _check(Bd, orc, net, scheme, 0.05, 12.0, 75, 11 + seed, station, tau0, 2, rep_begin=7)
+        _check(Bd, orc, net, scheme, 0.05, 12.0, 75, 11 + seed, station, tau0, 2, rep_begin=7,
+               options={Bd.OPT_FORM: form})
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_dag100_sojourn_parity(Bd, orc, scheme):
-    """The 100-station layered DAG, 70 replications x 300 steps."""
+def test_dag100_sojourn_parity(Bd, orc, scheme, form):
+    """The 100-station layered DAG, 70 replications x 300 steps, both forms."""
     run = W.layered_dag()
-    _check(Bd, orc, run.net, scheme, run.dt, 3.0, 70, run.seed, 3, 20, 2)
+    _check(Bd, orc, run.net, scheme, run.dt, 3.0, 70, run.seed, 3, 20, 2, options={Bd.OPT_FORM: form})
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_sojourn_with_staffing_and_departure_variants(Bd, orc, scheme):
-    """The staffing-schedule and Eq. (1)/(2) instantiations of the kernel."""
+def test_sojourn_with_staffing_and_departure_variants(Bd, orc, scheme, form):
+    """The staffing-schedule and Eq. (1)/(2) instantiations of the kernels."""
     rng = np.random.default_rng(21)
     net = W.random_small_dag(rng, 7, max_deg=2, m_range=(1, 8), ext_frac=0.6, lam_scale=5.0)
     net.servers_schedule = rng.integers(1, 9, size=(4, net.n)).astype(np.int32)
     net.servers_schedule_dt = 1.5
-    _check(Bd, orc, net, scheme, 0.05, 8.0, 64, 5, 0, 10, 2)
+    _check(Bd, orc, net, scheme, 0.05, 8.0, 64, 5, 0, 10, 2, options={Bd.OPT_FORM: form})
     net.servers_schedule = None
     for mode in (1, 2):
         old = orc.set_departure_mode(mode)
         try:
             _check(Bd, orc, net, scheme, 0.05, 8.0, 40, 6, 0, 10, 2,
-                   options={Bd.OPT_DEPARTURE: mode})
+                   options={Bd.OPT_DEPARTURE: mode, Bd.OPT_FORM: form})
         finally:
             orc.set_departure_mode(old)
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_sojourn_edge_cases(Bd, orc, scheme):
+def test_sojourn_edge_cases(Bd, orc, scheme, form):
     """Entry in the last step (all censored, nothing accounted), entry in the
-    first step, many tagged customers (the tile shrinks below 32
+    first step, many tagged customers (the persistent tile shrinks below 32
     replications), and no replications at all."""
     import torch
     run = W.tandem3()
     K = Bd.num_steps(run.dt, 2.0)
-    got = _check(Bd, orc, run.net, scheme, run.dt, 2.0, 40, 4, 1, K, 3)
+    o = {Bd.OPT_FORM: form}
+    got = _check(Bd, orc, run.net, scheme, run.dt, 2.0, 40, 4, 1, K, 3, options=o)
     assert (got == 0).all()
-    _check(Bd, orc, run.net, scheme, run.dt, 2.0, 40, 4, 0, 1, 1)
-    _check(Bd, orc, run.net, scheme, run.dt, 1.0, 37, 4, 0, 30, 700)
+    _check(Bd, orc, run.net, scheme, run.dt, 2.0, 40, 4, 0, 1, 1, options=o)
+    _check(Bd, orc, run.net, scheme, run.dt, 1.0, 37, 4, 0, 30, 700, options=o)
     h = Bd.EulerNet(run.net)
     try:
         out = torch.empty((0, 2), dtype=torch.int32, device="cuda")
@@ -126,9 +136,9 @@ def test_sojourn_edge_cases(Bd, orc, scheme):
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_dag100_full_size_sojourn_sampled(Bd, orc, scheme):
     """The benchmark workload at full size (10,000 replications x 10,000
-    steps) with 4 tagged customers per replication entering station 0 at t =
-    50: sampled replications re-run by the oracle match exactly; the
-    statistics equal those of the plain simulation."""
+    steps; the planner's form) with 4 tagged customers per replication
+    entering station 0 at t = 50: sampled replications re-run by the oracle
+    match exactly; the statistics equal those of the plain simulation."""
     import torch
     run = W.layered_dag()
     h = Bd.EulerNet(run.net)
