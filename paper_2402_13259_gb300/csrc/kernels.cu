@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
 
 constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
 #ifndef EN_HBM_MIN_BLOCKS
-#define EN_HBM_MIN_BLOCKS 4  // resident 256-thread CTAs per SM the register budget targets
+#define EN_HBM_MIN_BLOCKS 5  // resident 256-thread CTAs per SM the register budget targets
 #endif
 
 // Units of one phase over stations lvl_station[s0 .. s0+m) (phases 2, 3) or

@@ -99,6 +99,9 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
                                                 SamplerCtx& cx, int32_t& D, int32_t& X, float& smu) {
   PhiloxStream svc;
   svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
+  // Block 0 of the stream now, while the warp's lanes still run together
+  // (the first draw would compute the same block inside a divergent branch).
+  svc.refill();
   const int32_t m = servers_at<EXT>(t, p, i, tau);
   const int32_t e0 = __ldg(t.row_ptr + i);
   const int32_t deg = __ldg(t.row_ptr + i + 1) - e0;
@@ -162,6 +165,7 @@ __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunPara
   if (ec >= 0) {
     PhiloxStream arr;
     arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
+    arr.refill();  // every Poisson draw takes at least one word
     const float lam = __ldg(lam_t + ec);
     o.A = poisson(lam, arr, cx);
     if (GRAD && lam > 0.0f) o.garr = (float)o.A / lam - 1.0f;  // d log Poisson / d Lambda * Lambda / Lambda
