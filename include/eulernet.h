@@ -297,12 +297,16 @@ enum {
                                 warps' bounded waits run out                  */
   EULER_OPT_WAIT_SLEEP = 9,  /* nanoseconds between polls of an inter-warp
                                 wait of the pipelined form (default 64)       */
-  EULER_OPT_DEPARTURE = 10   /* departure sampler: 0 = exact (Lemma 1,
+  EULER_OPT_DEPARTURE = 10,  /* departure sampler: 0 = exact (Lemma 1,
                                 Algorithm 1), 1 = Eq. (1) D = min(x,
                                 Poisson(min(x, m) mu h)), 2 = Eq. (2)
                                 (binomial for x <= m, Eq. (1) otherwise); the
                                 biased modes are for speed/bias studies and
                                 are not available to euler_net_grad           */
+  EULER_OPT_GRAD_CENTER = 11 /* euler_net_grad's estimator: 0 = mean of L S,
+                                1 = centred, mean of (L - mean L) S: the same
+                                expectation (E[S] = 0), lower variance when L
+                                varies little around a large mean             */
 };
 EULERNET_API int euler_net_set_option(euler_net* net, int32_t option, int64_t value);
 

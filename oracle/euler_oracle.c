@@ -28,6 +28,9 @@ void eo_counters_get(int64_t out[EOC_COUNT]) { memcpy(out, g_cnt, sizeof g_cnt);
 static int32_t g_cap = 1000;  /* rejection-loop iteration cap */
 int32_t eo_set_cap(int32_t cap) { int32_t o = g_cap; g_cap = cap > 0 ? cap : 1; return o; }
 
+static int32_t g_grad_center = 0;  /* eo_grad: 1 = centred estimator */
+int32_t eo_set_grad_center(int32_t on) { int32_t o = g_grad_center; g_grad_center = on ? 1 : 0; return o; }
+
 static int32_t g_dep_mode = 0;  /* 0 exact, 1 Eq. (1), 2 Eq. (2) */
 int32_t eo_set_departure_mode(int32_t mode) {
   int32_t o = g_dep_mode;
@@ -968,13 +971,15 @@ int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, u
         vsum += part;
       }
       value[m] = vsum / (double)R;
+      /* centred estimator: (L - mean L) S, same expectation since E[S] = 0 */
+      const double Lbar = g_grad_center ? value[m] : 0.0;
       for (int64_t c = 0; c < C; ++c) {
         double s = 0.0, ss = 0.0;
         for (int64_t b0 = 0; b0 < R; b0 += 32) {
           double part = 0.0, part2 = 0.0;
           for (int64_t r = b0; r < R && r < b0 + 32; ++r) {
             double L = m == 0 ? dt * (double)rp[4 * r] : (double)rp[4 * r + 1];
-            double x = L * sc[r * C + c];
+            double x = (g_grad_center ? L - Lbar : L) * sc[r * C + c];
             part += x;
             part2 += x * x;
           }

@@ -85,7 +85,8 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T,
                 int32_t* trace_N, int32_t* trace_D, int32_t* trace_A);
 
 /* Likelihood-ratio gradient of L1 = dt sum N and L2 = sum D with respect to
- * (mu_1..mu_n, a, b, phase) of the sinusoid arrivals; see euler_oracle.c.
+ * (mu_1..mu_n, a, b, phase) of the sinusoid arrivals (centred with
+ * eo_set_grad_center(1)); see euler_oracle.c.
  * grad, grad_var: [2][n+3]; value: [2]; scores_out: [R][n+3] or NULL. */
 int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
             int64_t rep_begin, double* scores_out, double* grad, double* value, double* grad_var);
@@ -102,6 +103,11 @@ int eo_sojourn(const eo_net* net, int32_t scheme, double dt, double T, int64_t R
 /* Lemma 3: P(the tagged customer's service continues through a step | the
  * step's departure draw had input x and output d, m servers). */
 float eo_sojourn_pstay(int32_t x, int32_t d, int32_t m);
+
+/* eo_grad's estimator: 0 = mean of L S (default), 1 = centred, mean of
+ * (L - mean L) S (the same expectation, as E[S] = 0; lower variance).
+ * Returns the previous setting. */
+int32_t eo_set_grad_center(int32_t on);
 
 /* Number of Euler steps for a horizon: K = ceil(T/dt - 1e-9). */
 int64_t eo_num_steps(double dt, double T);

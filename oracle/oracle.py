@@ -20,6 +20,7 @@ __all__ = [
     "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
     "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
     "BACKWARD", "FORWARD", "grad", "set_departure_mode", "sojourn", "sojourn_pstay", "des_simulate",
+    "set_grad_center",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -93,6 +94,8 @@ def lib():
         L.eo_counters_get.argtypes = [C.c_void_p]
         L.eo_set_departure_mode.restype = C.c_int32
         L.eo_set_departure_mode.argtypes = [C.c_int32]
+        L.eo_set_grad_center.argtypes = [C.c_int32]
+        L.eo_set_grad_center.restype = C.c_int32
         L.eo_grad.restype = C.c_int
         L.eo_des_simulate.argtypes = [C.POINTER(_Net), C.c_double, C.c_double, C.c_int64, C.c_uint64,
                                       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -245,6 +248,11 @@ def des_simulate(net: Network, dt: float, T: float, R: int, seed: int, rep_begin
 def sojourn_pstay(x: int, d: int, m: int) -> float:
     """Lemma 3's stay probability as the oracle evaluates it (float32)."""
     return float(lib().eo_sojourn_pstay(int(x), int(d), int(m)))
+
+
+def set_grad_center(on: bool) -> int:
+    """grad(): 1 = centred estimator mean((L - mean L) S); returns the old setting."""
+    return int(lib().eo_set_grad_center(1 if on else 0))
 
 
 def set_departure_mode(mode: int) -> int:

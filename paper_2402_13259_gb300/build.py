@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeulernet.so")
 SOURCES = ["kernels.cu", "pipeline.cu", "abi.cu", "noalloc.cu", "batch.cu", "sojourn.cu"]
-HEADERS = ["sampling.cuh", "internal.h", "handle.h", "unit.cuh", "tile.cuh", os.path.join("..", "..", "include", "eulernet.h")]
+HEADERS = ["sampling.cuh", "internal.h", "handle.h", "unit.cuh", "tile.cuh", "hbm_step.cuh", os.path.join("..", "..", "include", "eulernet.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 # extra nvcc arguments for tuning builds (e.g. "-DEN_HBM_MIN_BLOCKS=3"); the

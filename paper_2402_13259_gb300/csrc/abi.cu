@@ -646,7 +646,7 @@ int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t l
 }
 
 int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
-  if (!h || option < 0 || option > EULER_OPT_DEPARTURE) return fail(EULER_ERR_ARG, "bad option");
+  if (!h || option < 0 || option > EULER_OPT_GRAD_CENTER) return fail(EULER_ERR_ARG, "bad option");
   h->opt[option] = value < 0 ? -1 : value;
   return EULER_OK;
 }
@@ -852,7 +852,8 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
     xg.th_acc = h->d_gth;
     rc = run_hbm_form(h, h->tables(), p, pl.block, s, xg);
     if (rc) return rc;
-    cudaError_t e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var, s);
+    cudaError_t e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var,
+                                       h->opt[EULER_OPT_GRAD_CENTER] > 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
     return EULER_OK;
   }
@@ -904,7 +905,8 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
   CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(int64_t) * (size_t)euler_stats_len(h->n, R), s));
   e = launch_persistent_grad(h->tables(), p, grid, block, (int)smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
-  e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var, s);
+  e = launch_grad_reduce(h->n, R, dt, stats, scores, h->d_gpartial, grad, value, grad_var,
+                                       h->opt[EULER_OPT_GRAD_CENTER] > 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
   return EULER_OK;
 }

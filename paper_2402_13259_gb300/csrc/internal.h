@@ -72,7 +72,7 @@ cudaError_t launch_persistent_grad(const NetTables& t, const RunParams& p, int g
                                    int smem, cudaStream_t s);
 cudaError_t launch_grad_reduce(int32_t n, int64_t R, double dt, const int64_t* stats,
                                const double* scores, double* partial, double* grad, double* value,
-                               double* grad_var, cudaStream_t s);
+                               double* grad_var, bool center, cudaStream_t s);
 
 // out[k] = (b[k] + f[k]) / 2 in double.
 cudaError_t launch_average(const int64_t* b, const int64_t* f, double* out, int64_t len,

@@ -1,7 +1,7 @@
 """Likelihood-ratio gradients on the GPU: bit-for-bit equal to the CPU
-oracle's (per-replication scores, gradient, value, variance), consistent
-with central finite differences under common random numbers, and wired into
-torch.autograd."""
+oracle's (per-replication scores, gradient, value, variance; plain and
+centred estimators; both launch forms), consistent with central finite
+differences under common random numbers, and wired into torch.autograd."""
 import math
 
 import numpy as np
@@ -35,20 +35,27 @@ def _cases():
     return [(_queueing_net(), 0.3, 3.0, 300), (W.tandem3().net, 0.01, 2.0, 100), (dag, 0.05, 2.5, 70)]
 
 
+@pytest.mark.parametrize("center", [0, 1])
 @pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("case", range(3))
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_grad_matches_oracle_exactly(Bd, orc, case, scheme, form):
+def test_grad_matches_oracle_exactly(Bd, orc, case, scheme, form, center):
     """Persistent form (score sums in shared memory) and HBM form (score sums
-    per station and replication in global memory) both match the oracle."""
+    per station and replication in global memory) both match the oracle, for
+    the plain and the centred estimator."""
     net, dt, T, R = _cases()[case]
     h = Bd.EulerNet(net)
     try:
         h.set_option(Bd.OPT_FORM, form)
+        h.set_option(Bd.OPT_GRAD_CENTER, center)
         g = h.grad(scheme, dt, T, R, 31, rep_begin=5, scores=True, stats=True)
     finally:
         h.close()
-    want = orc.grad(net, scheme, dt, T, R, 31, rep_begin=5, scores=True)
+    old = orc.set_grad_center(center)
+    try:
+        want = orc.grad(net, scheme, dt, T, R, 31, rep_begin=5, scores=True)
+    finally:
+        orc.set_grad_center(old)
     assert np.array_equal(g["scores"].cpu().numpy(), want["scores"])
     assert np.array_equal(g["grad"].cpu().numpy(), want["grad"])
     assert np.array_equal(g["value"].cpu().numpy(), want["value"])
@@ -89,6 +96,14 @@ def test_grad_agrees_with_finite_differences(Bd):
     finally:
         h.close()
     lr, lr_se = g["grad"].cpu().numpy(), np.sqrt(g["var"].cpu().numpy())
+    h = Bd.EulerNet(net)
+    try:
+        h.set_option(Bd.OPT_GRAD_CENTER, 1)
+        gc = h.grad(1, dt, T, R, seed)
+    finally:
+        h.close()
+    lrc, lrc_se = gc["grad"].cpu().numpy(), np.sqrt(gc["var"].cpu().numpy())
+    assert np.median(lrc_se / lr_se) < 0.5  # the centred estimator's smaller errors
     for c in range(len(theta)):
         d = 1e-3 * max(abs(theta[c]), 0.1)
         vals = []
@@ -106,6 +121,8 @@ def test_grad_agrees_with_finite_differences(Bd):
         fd, fd_se = diff.mean(axis=1), diff.std(axis=1) / math.sqrt(R)
         z = (fd - lr[:, c]) / np.sqrt(fd_se ** 2 + lr_se[:, c] ** 2)
         assert np.all(np.abs(z) < 5.0), (c, fd, lr[:, c], z)
+        zc = (fd - lrc[:, c]) / np.sqrt(fd_se ** 2 + lrc_se[:, c] ** 2)
+        assert np.all(np.abs(zc) < 5.0), (c, fd, lrc[:, c], zc)
 
 
 def test_autograd_function(Bd):

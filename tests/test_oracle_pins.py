@@ -571,6 +571,18 @@ def test_gradient_matches_infinite_server_closed_form(orc, scheme):
     se = np.sqrt(g["var"])
     z = (g["grad"] - want) / np.maximum(se, 1e-12)
     assert np.abs(z).max() < 5.0, z
+    # the centred estimator, mean (L - mean L) S, estimates the same
+    # derivatives with smaller standard errors
+    old = orc.set_grad_center(1)
+    try:
+        gc = orc.grad(net, scheme, dt, K * dt, R, 23)
+    finally:
+        orc.set_grad_center(old)
+    assert np.array_equal(gc["value"], g["value"])
+    sec = np.sqrt(gc["var"])
+    zc = (gc["grad"] - want) / np.maximum(sec, 1e-12)
+    assert np.abs(zc).max() < 5.0, zc
+    assert (sec <= se).mean() > 0.9 and np.median(sec / np.maximum(se, 1e-300)) < 0.5
 
 
 # ---------------------------------------------------------------------------
