@@ -108,8 +108,12 @@ static const int32_t* servers_at_time(const eo_net* net, double t) {
   return net->sv_table + j * net->n;
 }
 
-int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t seed,
-                    int64_t rep_begin, int64_t* stats, int32_t* trace_N, int64_t* events) {
+/* The simulation; with tag_station >= 0 one tagged customer joins that
+ * station at time tag_t0 in every replication and its sojourn is written to
+ * tag_out[r] (-1 if it is still in the network at K dt). */
+static int des_run(const eo_net* net, double dt, double T, int64_t R, uint64_t seed,
+                   int64_t rep_begin, int64_t* stats, int32_t* trace_N, int64_t* events,
+                   int32_t tag_station, double tag_t0, double* tag_out) {
   if (!net || net->n < 1 || !net->row_ptr || !net->servers || !net->mu || !stats) return EO_ERR_ARG;
   if (!(dt > 0.0) || !(T > 0.0) || R < 0 || rep_begin < 0) return EO_ERR_ARG;
   const int32_t n = net->n;
@@ -149,6 +153,12 @@ int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t 
     double next_change = net->sv_table ? net->sv_dt : INFINITY;
     const int32_t* m = servers_at_time(net, 0.0);
     int64_t* sr = st_rep + 4 * r;
+    /* tagged customer: station (-1 before it joins / after it leaves) and its
+       place (customers ahead of it plus one; <= m: in service) */
+    int32_t tag_at = -1;
+    int64_t tag_pos = 0;
+    int tag_pending = tag_station >= 0;
+    if (tag_out) tag_out[r] = -1.0;
     for (;;) {
       double S = 0.0;
       for (int32_t i = 0; i < n; ++i) {
@@ -158,8 +168,13 @@ int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t 
       }
       const double Rtot = Lmax + S;
       double t_next = Rtot > 0.0 ? t - log(rng_u01(&g)) / Rtot : INFINITY;
-      const int change = next_change < t_next && next_change <= t_end;
-      const double t_stop = change ? next_change : t_next;
+      int change = next_change < t_next && next_change <= t_end;
+      double t_stop = change ? next_change : t_next;
+      const int join = tag_pending && tag_t0 < t_stop && tag_t0 <= t_end;
+      if (join) {  /* the tagged customer joins before the next event: redraw after */
+        change = 0;
+        t_stop = tag_t0;
+      }
       /* observations in (t, t_stop] see the current state */
       while (tau <= K && (double)tau * dt <= t_stop) {
         const int32_t* mo = servers_at_time(net, (double)tau * dt);
@@ -173,6 +188,14 @@ int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t 
         ++tau;
       }
       if (t_stop > t_end) break;
+      if (join) {
+        t = tag_t0;
+        tag_pending = 0;
+        tag_at = tag_station;
+        N[tag_at] += 1;
+        tag_pos = N[tag_at];
+        continue;
+      }
       if (change) {  /* staffing changes before the next event: redraw from there */
         t = next_change;
         next_change += net->sv_dt;
@@ -205,6 +228,17 @@ int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t 
           for (i = n - 1; i > 0 && srate[i] <= 0.0; --i) {
           }
         }
+        /* the tagged customer at this station: waiting, it moves up one place;
+           in service, the completion is its own with probability 1 / busy */
+        int tag_leaves = 0;
+        if (tag_at == i) {
+          const int64_t busy = N[i] < m[i] ? N[i] : m[i];
+          if (tag_pos > m[i]) {
+            tag_pos -= 1;
+          } else if (rng_u01(&g) * (double)busy < 1.0) {
+            tag_leaves = 1;
+          }
+        }
         N[i] -= 1;
         st_station[5 * (int64_t)i + 2] += 1;
         sr[1] += 1;
@@ -223,6 +257,15 @@ int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t 
           st_station[5 * (int64_t)i + 3] += 1;
           sr[2] += 1;
         }
+        if (tag_leaves) {
+          if (dest >= 0) {
+            tag_at = dest;
+            tag_pos = N[dest];
+          } else {
+            tag_at = -1;
+            if (tag_out) tag_out[r] = t - tag_t0;
+          }
+        }
       }
     }
     for (int32_t i = 0; i < n; ++i) st_NK[i] += N[i];
@@ -232,4 +275,19 @@ int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t 
   free(srate);
   free(N);
   return EO_OK;
+}
+
+int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t seed,
+                    int64_t rep_begin, int64_t* stats, int32_t* trace_N, int64_t* events) {
+  return des_run(net, dt, T, R, seed, rep_begin, stats, trace_N, events, -1, 0.0, NULL);
+}
+
+int eo_des_sojourn(const eo_net* net, double dt, double T, int64_t R, uint64_t seed,
+                   int64_t rep_begin, int32_t station, double t0, double* out, int64_t* stats) {
+  if (!net || station < 0 || station >= net->n || !(t0 >= 0.0) || !out) return EO_ERR_ARG;
+  if (net->sv_table) return EO_ERR_ARG;  /* constant staffing only */
+  int64_t* st = stats ? stats : (int64_t*)malloc((size_t)(6 * (int64_t)net->n + 4 * R) * sizeof(int64_t));
+  const int rc = des_run(net, dt, T, R, seed, rep_begin, st, NULL, NULL, station, t0, out);
+  if (!stats) free(st);
+  return rc;
 }

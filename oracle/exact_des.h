@@ -34,6 +34,15 @@ extern "C" {
 int eo_des_simulate(const eo_net* net, double dt, double T, int64_t R, uint64_t seed,
                     int64_t rep_begin, int64_t* stats, int32_t* trace_N, int64_t* events);
 
+/* Sojourn time of a tagged customer that joins `station` at time t0 in each
+ * replication (FCFS; exponential services, so a service completion at its
+ * station is its own with probability 1 / busy servers while it is in
+ * service; it follows the departing customer's routing draw).  out[r]: the
+ * time from t0 to its exit, or -1 if it is still in the network at K dt.
+ * Constant staffing only.  stats (optional): the run's statistics. */
+int eo_des_sojourn(const eo_net* net, double dt, double T, int64_t R, uint64_t seed,
+                   int64_t rep_begin, int32_t station, double t0, double* out, int64_t* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ __all__ = [
     "draw_poisson", "draw_binomial", "draw_gamma", "draw_normal", "draw_departure",
     "draw_route", "uniforms", "counters", "counters_reset", "set_cap", "COUNTER_NAMES",
     "BACKWARD", "FORWARD", "grad", "set_departure_mode", "sojourn", "sojourn_pstay", "des_simulate",
-    "set_grad_center",
+    "set_grad_center", "des_sojourn",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -99,6 +99,8 @@ def lib():
         L.eo_grad.restype = C.c_int
         L.eo_des_simulate.argtypes = [C.POINTER(_Net), C.c_double, C.c_double, C.c_int64, C.c_uint64,
                                       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.eo_des_sojourn.argtypes = [C.POINTER(_Net), C.c_double, C.c_double, C.c_int64, C.c_uint64,
+                                     C.c_int64, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]
         L.eo_sojourn.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
                                  C.c_uint64, C.c_int64, C.c_int32, C.c_int64, C.c_int32,
                                  C.c_void_p, C.c_void_p]
@@ -242,6 +244,20 @@ def des_simulate(net: Network, dt: float, T: float, R: int, seed: int, rep_begin
     out.update(stats_split(stats, n, R))
     if trace:
         out["N"] = tr
+    return out
+
+
+def des_sojourn(net: Network, dt: float, T: float, R: int, seed: int, station: int, t0: float,
+                rep_begin: int = 0) -> np.ndarray:
+    """Exact sojourn times of a tagged customer joining `station` at time t0
+    in each replication (see exact_des.h): [R] doubles, -1 if not out by K dt."""
+    L = lib()
+    s, keep = _make_net(net)
+    out = np.zeros(R, dtype=np.float64)
+    rc = L.eo_des_sojourn(C.byref(s), dt, T, R, seed, rep_begin, station, t0, _ptr(out), None)
+    del keep
+    if rc != 0:
+        raise RuntimeError(f"oracle eo_des_sojourn failed with code {rc}")
     return out
 
 

@@ -270,3 +270,44 @@ def test_relative_error_under_the_selection_rule(orc):
         assert re_b < mu * h + 4.5 * se and re_f < mu * h + 4.5 * se
         total.append(re_b + re_f)
     assert total[1] < 0.6 * total[0]
+
+
+def test_des_sojourn_exact_laws(orc):
+    """The DES's tagged customer: in a stationary FCFS M/M/1 queue an arriving
+    customer's sojourn is Exp(mu - lambda) (PASTA); through two infinite-server
+    stations with a routing split it is Exp(mu_1) plus, with probability p,
+    an independent Exp(mu_2)."""
+    lam, mu, R = 0.7, 1.0, 20000
+    run = W.single_station(1, mu, lam, 1.0, 200.0, R, 3, N0=2)
+    t = orc.des_sojourn(run.net, 1.0, 200.0, R, 9, 0, 60.0)
+    assert (t < 0).sum() == 0
+    assert stats.kstest(t, stats.expon(scale=1.0 / (mu - lam)).cdf).pvalue > 1e-4
+    p, mu1, mu2 = 0.4, 2.0, 0.5
+    row_ptr, col, prob = W.csr_from_edges(2, [(0, 1, p)])
+    net = W.Network(2, row_ptr, col, prob, np.full(2, 10 ** 6), np.array([mu1, mu2]),
+                    W.Arrivals(kind=W.ARR_SINUSOID, w=np.array([5.0, 0.0]), a=1.0, b=0.0))
+    t = orc.des_sojourn(net, 1.0, 200.0, R, 11, 0, 3.0)
+    x = np.linspace(0.05, 12, 40)
+    # P(T <= x) for the mixture (1-p) Exp(mu1) + p (Exp(mu1) + Exp(mu2))
+    hypo = (1 - p) * (1 - np.exp(-mu1 * x)) + p * (1 - (mu1 * np.exp(-mu2 * x) - mu2 * np.exp(-mu1 * x)) / (mu1 - mu2))
+    emp = (t[None, :] <= x[:, None]).mean(axis=1)
+    assert np.abs(emp - hypo).max() < 1.36 * 1.3 / math.sqrt(R) * 3, np.abs(emp - hypo).max()
+
+
+def test_sojourn_converges_to_exact(orc):
+    """Sec. 7.6: the sojourn-time law of Algorithm 4 approaches the exact one
+    (a tagged customer followed through the DES under FCFS) as h shrinks: the
+    KS distance and the error of the mean fall from h = 0.2 to h = 0.05."""
+    run = W.tandem3()
+    T, t0, R = 20.0, 5.0, 6000
+    d = orc.des_sojourn(run.net, 0.05, T, R, 7, 0, t0)
+    assert (d < 0).mean() < 0.002  # (nearly) every tagged customer left by T
+    se = d.std() / math.sqrt(R)
+    for scheme in (0, 1):
+        err, ks = {}, {}
+        for h in (0.2, 0.05):
+            e = orc.sojourn(run.net, scheme, h, T, R, 8, 0, int(round(t0 / h)))["steps"][:, 0] * h
+            err[h] = abs(e.mean() - d.mean())
+            ks[h] = stats.ks_2samp(e, d).statistic
+        assert ks[0.05] < 0.6 * ks[0.2] and ks[0.05] < 0.06, (scheme, ks)
+        assert err[0.05] < 0.5 * err[0.2] + 3 * se and err[0.05] < 0.1 + 4 * se, (scheme, err)

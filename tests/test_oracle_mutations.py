@@ -79,9 +79,15 @@ DES_MUTANTS = [
     ("des_no_thinning", "if (lmax[i] > 0.0 && rng_u01(&g) * lmax[i] < rate_at(net, i, t)) {",
      "if (lmax[i] > 0.0) {"),
     # service completions at rate N mu instead of min(N, m) mu
-    ("des_busy_uncapped", "const int64_t busy = N[i] < m[i] ? N[i] : m[i];", "const int64_t busy = N[i];"),
+    ("des_busy_uncapped", "const int64_t busy = N[i] < m[i] ? N[i] : m[i];\n        srate[i]",
+     "const int64_t busy = N[i];\n        srate[i]"),
     # routing ignores the probabilities: always the first edge
     ("des_route_first_edge", "if (v < net->prob[e]) {", "if (v < 2.0) {"),
+    # tagged customer: its own completion taken with probability 1 / N, not 1 / busy
+    ("des_tag_departure", "} else if (rng_u01(&g) * (double)busy < 1.0) {",
+     "} else if (rng_u01(&g) * (double)N[i] < 1.0) {"),
+    # tagged customer: a waiting place that never moves up
+    ("des_tag_queue", "            tag_pos -= 1;", "            tag_pos -= 0;"),
 ]
 
 CASES = ([(n, "euler_oracle.c", o, w, "test_oracle_pins.py") for n, o, w in MUTANTS] +
