@@ -30,6 +30,14 @@
 #define EN_HD inline
 #define EN_D inline
 #endif
+// Rarely taken sampler paths (rejection samplers for large means, Erlang
+// times) are inlined like the rest unless EN_COLD_OUTLINE is defined (one
+// out-of-line copy each: smaller code, but calls and more spills).
+#if defined(__CUDACC__) && defined(EN_COLD_OUTLINE)
+#define EN_COLD static __device__ __noinline__
+#else
+#define EN_COLD EN_D
+#endif
 // The Philox block function is inlined at every draw site unless
 // EN_PHILOX_OUTLINE is defined (one out-of-line copy: smaller code).
 #if defined(__CUDACC__) && defined(EN_PHILOX_OUTLINE)
@@ -302,23 +310,8 @@ EN_D float log_binom_pmf(int k, int n, float p, float q) {
 // ---------------------------------------------------------------------------
 // Samplers.
 // ---------------------------------------------------------------------------
-EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
-  if (!(lam > 0.0f)) return 0;
-  if (lam < 10.0f) {
-    const float u = st.uniform();
-    float p = fm::exp(-lam);
-    float F = p;
-    int32_t k = 0;
-    while (u > F) {
-      if (k == 63) break;
-      k = k + 1;
-      p = (p * lam) * cx.rinv[k];
-      const float Fn = F + p;
-      if (Fn == F) break;
-      F = Fn;
-    }
-    return k;
-  }
+// Hoermann's PTRS for lam >= 10.
+EN_COLD int32_t poisson_ptrs(float lam, PhiloxStream& st, SamplerCtx& cx) {
   const float slam = sqrtf(lam);
   const float b = 0.931f + 2.53f * slam;
   const float a = -0.059f + 0.02483f * b;
@@ -338,6 +331,26 @@ EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
   }
   cx.err |= kErrSamplerCap;
   return (int32_t)floorf(lam);
+}
+
+EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
+  if (!(lam > 0.0f)) return 0;
+  if (lam < 10.0f) {
+    const float u = st.uniform();
+    float p = fm::exp(-lam);
+    float F = p;
+    int32_t k = 0;
+    while (u > F) {
+      if (k == 63) break;
+      k = k + 1;
+      p = (p * lam) * cx.rinv[k];
+      const float Fn = F + p;
+      if (Fn == F) break;
+      F = Fn;
+    }
+    return k;
+  }
+  return poisson_ptrs(lam, st, cx);
 }
 
 // Constants of one binomial success probability p, as the sampler uses them:
@@ -371,27 +384,10 @@ EN_HD BinomConst binom_const(float p) {
   return b;
 }
 
-// Bin(n, pe) for pe <= 1/2, q = 1 - pe: inversion for n pe < 10 (using r and
-// lq), BTRS otherwise.
-EN_D int32_t binomial_half(int32_t n, float p, float q, float r, float lq, PhiloxStream& st,
-                           SamplerCtx& cx) {
+// Hoermann's BTRS for Bin(n, p), p <= 1/2, n p >= 10.
+EN_COLD int32_t binomial_btrs(int32_t n, float p, float q, PhiloxStream& st, SamplerCtx& cx) {
   const float nf = (float)n;
   const float np = nf * p;
-  if (np < 10.0f) {
-    float pk = fm::exp(nf * lq);
-    float F = pk;
-    const float u = st.uniform();
-    int32_t k = 0;
-    while (u > F) {
-      if (k == n || k == 63) break;
-      pk = ((pk * (float)(n - k)) * r) * cx.rinv[k + 1];
-      k = k + 1;
-      const float Fn = F + pk;
-      if (Fn == F) break;
-      F = Fn;
-    }
-    return k;
-  }
   const float spq = sqrtf(np * q);
   const float b = 1.15f + 2.53f * spq;
   const float a = -0.0873f + 0.0248f * b + 0.01f * p;
@@ -414,6 +410,30 @@ EN_D int32_t binomial_half(int32_t n, float p, float q, float r, float lq, Philo
   }
   cx.err |= kErrSamplerCap;
   return (int32_t)floorf(np);
+}
+
+// Bin(n, pe) for pe <= 1/2, q = 1 - pe: inversion for n pe < 10 (using r and
+// lq), BTRS otherwise.
+EN_D int32_t binomial_half(int32_t n, float p, float q, float r, float lq, PhiloxStream& st,
+                           SamplerCtx& cx) {
+  const float nf = (float)n;
+  const float np = nf * p;
+  if (np < 10.0f) {
+    float pk = fm::exp(nf * lq);
+    float F = pk;
+    const float u = st.uniform();
+    int32_t k = 0;
+    while (u > F) {
+      if (k == n || k == 63) break;
+      pk = ((pk * (float)(n - k)) * r) * cx.rinv[k + 1];
+      k = k + 1;
+      const float Fn = F + pk;
+      if (Fn == F) break;
+      F = Fn;
+    }
+    return k;
+  }
+  return binomial_btrs(n, p, q, st, cx);
 }
 
 // Bin(n, p) from its constants: zero draws if n = 0 or p <= 0 (Appendix A's
@@ -445,7 +465,7 @@ EN_D float std_normal(PhiloxStream& st, SamplerCtx& cx) {
   return 0.0f;
 }
 
-EN_D float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
+EN_COLD float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
   if (k <= 0) return 0.0f;
   if (k <= 8) {
     float S = 0.0f;
