@@ -189,6 +189,21 @@ def cpu_baseline(run, K_full, reps=12):
                       f"(single-threaded C oracle)", "seconds": total_t, "des": des}, per_scheme
 
 
+def op_counts(run, K_full, reps=1):
+    """Algorithmic operations per unit of both schemes from the oracle's event
+    counters on a small sample (no timing)."""
+    from oracle import oracle as O
+    from paper_2402_13259_gb300 import opmodel
+    per_scheme = {}
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        O.counters_reset()
+        O.simulate(run.net, scheme, run.dt, run.T, reps, run.seed, rep_begin=0)
+        c = O.counters()
+        per_scheme[name] = {"ops_per_unit": opmodel.ops_per_unit(c),
+                            "philox_blocks_per_unit": c["philox_blocks"] / max(c["units"], 1)}
+    return per_scheme
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, a bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -287,7 +302,7 @@ def run_rows(args):
     scheme, sojourn times, a staffing schedule, the Eq. (1)/(2) departure
     samplers, likelihood-ratio gradients (100,000 replications of the
     sinusoid-arrival DAG) and the staffing-scale sweep (2,000 stations,
-    dt = 1/sqrt(s), 2,048 replications).  One JSON line per row; bit-exact
+    dt = 1/sqrt(s); 100,000 replications for s <= 100, 16,384 above).  One JSON line per row; bit-exact
     parity of each row is in the GPU tests."""
     import numpy as np
     import torch
@@ -390,9 +405,10 @@ def run_rows(args):
              "euler_net_grad", "tests/test_gpu_grad.py")
     hg.status()
     hg.close()
-    # C2: staffing-scale sweep (2,000 stations), reduced replications
+    # C2: staffing-scale sweep (2,000 stations); the full 100,000 replications
+    # where a call takes seconds, 16,384 (already 3.3e7 units per step) above
     for sc in (10, 100, 1000, 10000):
-        rs = W.scale_dag(sc, R=2048)
+        rs = W.scale_dag(sc, R=100000 if sc <= 100 else 16384)
         hc = Bd.EulerNet(rs.net)
         Ks = Bd.num_steps(rs.dt, rs.T)
         st2 = torch.empty(Bd.stats_len(rs.net.n, rs.R), dtype=torch.int64, device="cuda")
@@ -523,8 +539,10 @@ def main():
         return 0
 
     base, per_scheme = (None, None)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         base, per_scheme = cpu_baseline(run, K)
+    elif not args.no_cpu_baseline:
+        per_scheme = op_counts(run, K)  # the roofline's operation counts only
     units_launch = n * K * R
     roof = None
     if per_scheme:

@@ -303,10 +303,15 @@ enum {
                                 (binomial for x <= m, Eq. (1) otherwise); the
                                 biased modes are for speed/bias studies and
                                 are not available to euler_net_grad           */
-  EULER_OPT_GRAD_CENTER = 11 /* euler_net_grad's estimator: 0 = mean of L S,
+  EULER_OPT_GRAD_CENTER = 11, /* euler_net_grad's estimator: 0 = mean of L S,
                                 1 = centred, mean of (L - mean L) S: the same
                                 expectation (E[S] = 0), lower variance when L
                                 varies little around a large mean             */
+  EULER_OPT_HBM_CHUNK = 12   /* HBM form: replications run together over the
+                                whole horizon before the next chunk (default:
+                                as many as keep the state within ~64 MiB of
+                                L2, at least 2^18 / n); results do not depend
+                                on it                                          */
 };
 EULERNET_API int euler_net_set_option(euler_net* net, int32_t option, int64_t value);
 

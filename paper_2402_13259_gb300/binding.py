@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libeulernet.so")
 
 BACKWARD, FORWARD = 0, 1
 (OPT_FORM, OPT_TILE_REPS, OPT_BLOCK, OPT_GRID, OPT_SAMPLER_CAP, OPT_GRAPH_STEPS, OPT_PIPE_WARPS,
- OPT_WAIT_LIMIT, OPT_TEST_STALL, OPT_WAIT_SLEEP, OPT_DEPARTURE, OPT_GRAD_CENTER) = range(12)
+ OPT_WAIT_LIMIT, OPT_TEST_STALL, OPT_WAIT_SLEEP, OPT_DEPARTURE, OPT_GRAD_CENTER, OPT_HBM_CHUNK) = range(13)
 
 ERRORS = {
     -1: "EULER_ERR_ARG", -2: "EULER_ERR_NOT_FEEDFORWARD", -3: "EULER_ERR_CUDA", -4: "EULER_ERR_OOM",

@@ -349,7 +349,22 @@ int64_t hbm_slots(const euler_net* h, int32_t scheme, int64_t K) {
 // to x.out.
 int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p, int block,
                            cudaStream_t s, const HbmExtra& x) {
-  int rc = ensure_hbm_state(h, p.R);
+  int rc = ensure_levels(h);
+  if (rc) return rc;
+  // Replications in chunks whose state (N, the routed-count ring, the
+  // per-replication sums and the mode's extra sums) fits in about
+  // kHbmL2Budget bytes of L2, whole horizon per chunk: counter-based keying
+  // makes the results those of one pass.  A chunk keeps n x R >= 2^18 units
+  // per step.
+  const int64_t per_rep = 4 * ((int64_t)h->n + std::max(h->hbm_depth, 2) * (int64_t)h->E) + 32 +
+                          (x.mode == kHbmGrad ? 8 * ((int64_t)h->n + 3 * (int64_t)std::max(h->n_ex, 1)) : 0) +
+                          (x.mode == kHbmSojourn ? 16 * (int64_t)x.S : 0);
+  int64_t Rc = h->opt[EULER_OPT_HBM_CHUNK] > 0
+                   ? h->opt[EULER_OPT_HBM_CHUNK]
+                   : std::max<int64_t>(kHbmL2Budget / per_rep, (kHbmMinUnitsPerStep + h->n - 1) / h->n);
+  Rc = (Rc + 31) / 32 * 32;
+  if (Rc > p.R) Rc = p.R;
+  rc = ensure_hbm_state(h, Rc);
   if (rc) return rc;
   HbmState hs;
   hs.N = h->d_N;
@@ -366,40 +381,47 @@ int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p,
   hs.csteps = x.csteps;
   hs.col = x.col;
   hs.S = x.S;
-  if (x.mode == kHbmGrad) {
-    CUDA_TRY(cudaMemsetAsync(x.mu_acc, 0, sizeof(double) * (size_t)h->n * hs.ld, s));
-    CUDA_TRY(cudaMemsetAsync(x.th_acc, 0, sizeof(double) * (size_t)std::max(h->n_ex, 1) * 3 * hs.ld, s));
-  }
-  if (x.mode == kHbmSojourn) CUDA_TRY(launch_hbm_sojourn_init(p, hs, x.station, x.tau0, s));
-  CUDA_TRY(launch_hbm_init(t, p, hs, s));
   // backward: K + 1 fused slots; forward: K + L - 1 skewed slots
   const int64_t slots = hbm_slots(h, p.scheme, p.K);
   const int64_t S = h->opt[EULER_OPT_GRAPH_STEPS] > 0 ? h->opt[EULER_OPT_GRAPH_STEPS]
                                                       : std::min<int64_t>(slots, 32);
   if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int64_t k = 0; k <= S; ++k) {
-    cudaError_t e = k < S ? launch_hbm_slot(t, p, hs, block, (int32_t)k, x.mode, h->cap_stream)
-                          : launch_hbm_advance(hs, (int32_t)S, h->cap_stream);
-    if (e != cudaSuccess) {
-      cudaStreamEndCapture(h->cap_stream, &graph);
-      if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(e, "hbm step capture");
+  for (int64_t r0 = 0; r0 < p.R; r0 += Rc) {
+    RunParams pc = p;
+    pc.R = std::min<int64_t>(Rc, p.R - r0);
+    pc.rep_begin = p.rep_begin + r0;
+    pc.num_tiles = (pc.R + 31) / 32;
+    if (x.mode == kHbmGrad) {
+      pc.scores = p.scores + r0 * ((int64_t)h->n + 3);
+      CUDA_TRY(cudaMemsetAsync(x.mu_acc, 0, sizeof(double) * (size_t)h->n * hs.ld, s));
+      CUDA_TRY(cudaMemsetAsync(x.th_acc, 0, sizeof(double) * (size_t)std::max(h->n_ex, 1) * 3 * hs.ld, s));
     }
+    if (x.mode == kHbmSojourn) CUDA_TRY(launch_hbm_sojourn_init(pc, hs, x.station, x.tau0, s));
+    CUDA_TRY(launch_hbm_init(t, pc, hs, s));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int64_t k = 0; k <= S; ++k) {
+      cudaError_t e = k < S ? launch_hbm_slot(t, pc, hs, block, (int32_t)k, x.mode, h->cap_stream)
+                            : launch_hbm_advance(hs, (int32_t)S, h->cap_stream);
+      if (e != cudaSuccess) {
+        cudaStreamEndCapture(h->cap_stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "hbm step capture");
+      }
+    }
+    CUDA_TRY(cudaStreamEndCapture(h->cap_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    const int64_t replays = (slots + S - 1) / S;
+    for (int64_t k = 0; k < replays && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    CUDA_TRY(launch_hbm_finish(t, pc, hs, p.R, r0, s));
+    if (x.mode == kHbmGrad) CUDA_TRY(launch_hbm_scores(t, pc, hs, s));
+    if (x.mode == kHbmSojourn) CUDA_TRY(launch_hbm_sojourn_finish(pc, hs, x.out + r0 * x.S, s));
   }
-  CUDA_TRY(cudaStreamEndCapture(h->cap_stream, &graph));
-  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  const int64_t replays = (slots + S - 1) / S;
-  for (int64_t k = 0; k < replays && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
-  cudaGraphExecDestroy(exec);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-  CUDA_TRY(launch_hbm_finish(t, p, hs, s));
-  if (x.mode == kHbmGrad) CUDA_TRY(launch_hbm_scores(t, p, hs, s));
-  if (x.mode == kHbmSojourn) CUDA_TRY(launch_hbm_sojourn_finish(p, hs, x.out, s));
   return EULER_OK;
 }
 
@@ -646,7 +668,7 @@ int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t l
 }
 
 int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
-  if (!h || option < 0 || option > EULER_OPT_GRAD_CENTER) return fail(EULER_ERR_ARG, "bad option");
+  if (!h || option < 0 || option > EULER_OPT_HBM_CHUNK) return fail(EULER_ERR_ARG, "bad option");
   h->opt[option] = value < 0 ? -1 : value;
   return EULER_OK;
 }

@@ -77,7 +77,7 @@ struct euler_net {
   int64_t hbm_cap_ld = 0, hbm_cap_R = 0;
   cudaStream_t cap_stream = nullptr;
 
-  int64_t opt[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+  int64_t opt[13] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
   int64_t h2d_bytes = 0;  // host-to-device bytes copied by this handle so far
 
   int32_t dep_mode() const { return opt[EULER_OPT_DEPARTURE] > 0 ? (int32_t)opt[EULER_OPT_DEPARTURE] : 0; }
@@ -109,6 +109,8 @@ namespace eulernet {
 // default threads per block.
 constexpr int64_t kHbmMinUnitsPerStep = int64_t(1) << 18;
 constexpr int kHbmBlock = 256;
+// Bytes of HBM-form state per replication chunk, so that a chunk stays in L2.
+constexpr int64_t kHbmL2Budget = int64_t(64) << 20;
 
 // What an HBM-form run computes besides the statistics (see HbmMode).
 struct HbmExtra {

@@ -146,6 +146,6 @@ cudaError_t launch_hbm_scores(const NetTables& t, const RunParams& p, const HbmS
                               cudaStream_t s);
 cudaError_t launch_hbm_advance(const HbmState& hs, int32_t by, cudaStream_t s);
 cudaError_t launch_hbm_finish(const NetTables& t, const RunParams& p, const HbmState& hs,
-                              cudaStream_t s);
+                              int64_t R_total, int64_t r0, cudaStream_t s);
 
 }  // namespace eulernet

@@ -202,8 +202,10 @@ __global__ void hbm_init_kernel(NetTables t, RunParams p, HbmState hs) {
 
 // Per-replication sums out, and N_K summed over replications (one block per
 // station, 128-bit loads of the replication-fastest state).
-__global__ void hbm_finish_kernel(NetTables t, RunParams p, HbmState hs) {
-  int64_t* st_rep = p.stats + 5 * (int64_t)t.n;
+// The replications of this call are rows r0 .. r0 + p.R of a stats layout for
+// R_total replications (chunked runs); N_K accumulates over the chunks.
+__global__ void hbm_finish_kernel(NetTables t, RunParams p, HbmState hs, int64_t R_total, int64_t r0) {
+  int64_t* st_rep = p.stats + 5 * (int64_t)t.n + 4 * r0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * p.R;
        k += (int64_t)gridDim.x * blockDim.x)
     st_rep[k] = hs.racc[k];
@@ -223,7 +225,7 @@ __global__ void hbm_finish_kernel(NetTables t, RunParams p, HbmState hs) {
     if (threadIdx.x == 0) {
       long long tot = 0;
       for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += part[k];
-      p.stats[5 * (int64_t)t.n + 4 * p.R + i] = tot;
+      p.stats[5 * (int64_t)t.n + 4 * R_total + i] += tot;
     }
     __syncthreads();
   }
@@ -467,8 +469,8 @@ cudaError_t launch_hbm_advance(const HbmState& hs, int32_t by, cudaStream_t s) {
 }
 
 cudaError_t launch_hbm_finish(const NetTables& t, const RunParams& p, const HbmState& hs,
-                              cudaStream_t s) {
-  hbm_finish_kernel<<<t.n < 1024 ? t.n : 1024, 256, 0, s>>>(t, p, hs);
+                              int64_t R_total, int64_t r0, cudaStream_t s) {
+  hbm_finish_kernel<<<t.n < 1024 ? t.n : 1024, 256, 0, s>>>(t, p, hs, R_total, r0);
   return cudaGetLastError();
 }
 

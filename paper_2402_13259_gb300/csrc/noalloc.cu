@@ -207,7 +207,7 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   e = launch_hbm_init(t, p, hs, s);  // N = N0, partial sums = 0, tau = 1
   for (int64_t k = 0; k < K && e == cudaSuccess; ++k)
     e = launch_hbm_step(t, p, hs, 256, h->lvl_ptr.data(), s);
-  if (e == cudaSuccess) e = launch_hbm_finish(t, p, hs, s);
+  if (e == cudaSuccess) e = launch_hbm_finish(t, p, hs, p.R, 0, s);
   if (e == cudaSuccess) {
     fold_error_kernel<<<1, 1, 0, s>>>(d_err, h->d_err);  // report through euler_net_status
     e = cudaGetLastError();

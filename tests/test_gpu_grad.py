@@ -48,6 +48,7 @@ def test_grad_matches_oracle_exactly(Bd, orc, case, scheme, form, center):
     try:
         h.set_option(Bd.OPT_FORM, form)
         h.set_option(Bd.OPT_GRAD_CENTER, center)
+        h.set_option(Bd.OPT_HBM_CHUNK, 64 if center else 0)  # chunked runs too
         g = h.grad(scheme, dt, T, R, 31, rep_begin=5, scores=True, stats=True)
     finally:
         h.close()

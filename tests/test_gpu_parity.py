@@ -116,13 +116,14 @@ def test_small_networks_parity(Bd, orc, case, scheme):
 def test_small_networks_hbm_form_parity(Bd, orc, case, scheme):
     """The HBM form on the same cases: skip edges across several levels make
     the skewed forward scheme keep routed counts for more than one step
-    (ring depth > 2); one and five steps per graph replay."""
+    (ring depth > 2); one and five steps per graph replay; replications run
+    in chunks of 32 (several chunks and a ragged one)."""
     net, R, dt, T = _small_cases()[case]
     want = orc.simulate(net, scheme, dt, T, R, 1000 + case)["stats"]
-    for steps in (1, 5):
+    for steps, chunk in ((1, 0), (5, 0), (5, 32)):
         got = _gpu_stats(Bd, net, scheme, dt, T, R, 1000 + case,
-                         options={Bd.OPT_FORM: 2, Bd.OPT_GRAPH_STEPS: steps})
-        _assert_equal(got, want, f"hbm case {case} scheme {scheme} graph steps {steps}")
+                         options={Bd.OPT_FORM: 2, Bd.OPT_GRAPH_STEPS: steps, Bd.OPT_HBM_CHUNK: chunk})
+        _assert_equal(got, want, f"hbm case {case} scheme {scheme} graph steps {steps} chunk {chunk}")
 
 
 @pytest.mark.parametrize("scheme", [0, 1])
@@ -162,6 +163,21 @@ def test_hbm_form_parity(Bd, orc, scheme):
     got = _gpu_stats(Bd, run.net, scheme, run.dt, 3.0, run.R, 3, options={Bd.OPT_FORM: 2})
     want = orc.simulate(run.net, scheme, run.dt, 3.0, run.R, 3)["stats"]
     _assert_equal(got, want, "hbm form")
+
+
+@pytest.mark.parametrize("s", [10, 100])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_scale_dag_full_size_sampled(Bd, orc, s, scheme):
+    """The scale sweep's 2,000-station DAG at its full size, 100,000
+    replications over the full horizon (s = 10: K = 159; s = 100: K = 500):
+    sampled replications re-run by the oracle, invariants over all."""
+    run = W.scale_dag(s)
+    got = _gpu_stats(Bd, run.net, scheme, run.dt, run.T, run.R, run.seed)
+    _invariants(Bd, got, run.net, run.R)
+    rp = Bd.split_stats(got, run.net.n, run.R)["rep"]
+    for r in (0, 54321, run.R - 1):
+        want = orc.simulate(run.net, scheme, run.dt, run.T, 1, run.seed, rep_begin=r)["rep"][0]
+        _assert_equal(rp[r], want, f"scale {s} replication {r}")
 
 
 @pytest.mark.parametrize("s", [10, 10000])

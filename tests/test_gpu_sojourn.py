@@ -78,7 +78,7 @@ def test_random_dag_sojourn_parity(Bd, orc, scheme, seed, form):
     net.N0 = rng.integers(0, 12, size=net.n).astype(np.int32)
     for station, tau0 in [(0, 1), (int(rng.integers(0, net.n)), 37), (net.n - 1, 150)]:
         _check(Bd, orc, net, scheme, 0.05, 12.0, 75, 11 + seed, station, tau0, 2, rep_begin=7,
-               options={Bd.OPT_FORM: form})
+               options={Bd.OPT_FORM: form, Bd.OPT_HBM_CHUNK: 32 if seed == 8 else 0})
 
 
 @pytest.mark.parametrize("form", [1, 2])
