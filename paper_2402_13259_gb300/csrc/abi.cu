@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -522,7 +523,7 @@ void euler_net_destroy(euler_net* h) {
 
 int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const int32_t* col,
                      const double* prob, const int32_t* servers, const double* mu,
-                     const euler_arrivals* arrivals, const int32_t* N0) {
+                     const euler_arrivals* arrivals, const int32_t* N0) try {
   if (!out) return fail(EULER_ERR_ARG, "out is NULL");
   *out = nullptr;
   int rc = validate_net(n, row_ptr, col, prob, servers, mu, arrivals, N0);
@@ -645,11 +646,15 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
   }
   *out = h;
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 int64_t euler_net_h2d_bytes(const euler_net* h) { return h ? h->h2d_bytes : -1; }
 
-int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t len, double tab_dt) {
+int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t len, double tab_dt) try {
   if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
   if (!table || len <= 0) {
     h->sv_table.clear();
@@ -665,6 +670,10 @@ int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t l
   h->c_dt = h->c_T = -1.0;  // rebuild the per-step tables on the next call
   h->g_dt = h->g_T = -1.0;
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
@@ -674,7 +683,7 @@ int euler_net_set_option(euler_net* h, int32_t option, int64_t value) {
 }
 
 int euler_net_plan(euler_net* h, int32_t scheme, int64_t R, int32_t* form, int32_t* tile_reps,
-                   int32_t* block, int32_t* grid, int32_t* smem_bytes) {
+                   int32_t* block, int32_t* grid, int32_t* smem_bytes) try {
   if (!h || R < 1) return fail(EULER_ERR_ARG, "bad plan arguments");
   Plan pl;
   int rc = make_plan(h, scheme, R, &pl);
@@ -685,10 +694,14 @@ int euler_net_plan(euler_net* h, int32_t scheme, int64_t R, int32_t* form, int32
   if (grid) *grid = pl.grid;
   if (smem_bytes) *smem_bytes = (int32_t)pl.smem;
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
-                       int64_t rep_begin, int64_t* stats, void* stream) {
+                       int64_t rep_begin, int64_t* stats, void* stream) try {
   if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
   if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return fail(EULER_ERR_ARG, "unknown scheme");
   if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T)) return fail(EULER_ERR_ARG, "dt and T must be finite and > 0");
@@ -738,6 +751,10 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
     return EULER_OK;
   }
   return run_hbm_form(h, t, p, pl.block, s, HbmExtra());
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 }  // extern "C"
@@ -803,7 +820,7 @@ extern "C" {
 
 int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
                    int64_t rep_begin, double* grad, double* value, double* grad_var, double* scores,
-                   int64_t* stats, void* stream) {
+                   int64_t* stats, void* stream) try {
   if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
   if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return fail(EULER_ERR_ARG, "unknown scheme");
   if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T)) return fail(EULER_ERR_ARG, "dt and T must be finite and > 0");
@@ -931,11 +948,15 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
                                        h->opt[EULER_OPT_GRAD_CENTER] > 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 int euler_net_simulate_average(euler_net* h, double dt, double T, int64_t R, uint64_t seed,
                                int64_t rep_begin, double* stats_avg, int64_t* stats_b,
-                               int64_t* stats_f, void* stream) {
+                               int64_t* stats_f, void* stream) try {
   if (!h || !stats_avg || R < 0) return fail(EULER_ERR_ARG, "bad average-scheme arguments");
   const size_t len = (size_t)euler_stats_len(h->n, R);
   if (!stats_b || !stats_f) {
@@ -958,6 +979,10 @@ int euler_net_simulate_average(euler_net* h, double dt, double T, int64_t R, uin
                                  reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "average kernel launch");
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 double euler_net_select_dt(const euler_net* h, double alpha) {
@@ -986,7 +1011,7 @@ int euler_net_status(euler_net* h, void* stream) {
 }
 
 int euler_net_simulate_host(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
-                            uint64_t seed, int64_t rep_begin, int64_t* stats_host, void* stream) {
+                            uint64_t seed, int64_t rep_begin, int64_t* stats_host, void* stream) try {
   if (!h || !stats_host) return fail(EULER_ERR_ARG, "handle or stats is NULL");
   const size_t bytes = sizeof(int64_t) * (size_t)euler_stats_len(h->n, R);
   int64_t* d_stats = nullptr;
@@ -1000,6 +1025,10 @@ int euler_net_simulate_host(euler_net* h, int32_t scheme, double dt, double T, i
   const int st = euler_net_status(h, stream);
   cudaFree(d_stats);
   return rc ? rc : st;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
 }  // extern "C"

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -223,7 +224,7 @@ cudaError_t enqueue(euler_batch* b, int64_t* const* stats, cudaStream_t s) {
 extern "C" {
 
 int euler_batch_create(euler_batch** out, euler_net* const* nets, const euler_run* runs,
-                       int32_t count) {
+                       int32_t count) try {
   if (!out) return bfail(EULER_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (count < 0 || (count > 0 && (!nets || !runs))) return bfail(EULER_ERR_ARG, "bad batch arguments");
@@ -268,9 +269,13 @@ int euler_batch_create(euler_batch** out, euler_net* const* nets, const euler_ru
   }
   *out = b;
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return bfail(EULER_ERR_CUDA, "unexpected error");
 }
 
-int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) {
+int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) try {
   if (!b) return bfail(EULER_ERR_ARG, "batch is NULL");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   // scratch stats buffers for the trial runs
@@ -323,9 +328,13 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
   if (rc) return rc;
   if (block_out) *block_out = b->block;
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return bfail(EULER_ERR_CUDA, "unexpected error");
 }
 
-int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) {
+int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) try {
   if (!b || (b->count > 0 && !stats)) return bfail(EULER_ERR_ARG, "bad batch run arguments");
   for (int j = 0; j < b->count; ++j)
     if (!stats[j]) return bfail(EULER_ERR_ARG, "a stats pointer is NULL");
@@ -355,6 +364,10 @@ int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) {
   }
   BTRY(cudaGraphLaunch(b->exec, s));
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return bfail(EULER_ERR_CUDA, "unexpected error");
 }
 
 int euler_batch_status(euler_batch* b, void* cuda_stream) {
@@ -380,7 +393,7 @@ void euler_batch_destroy(euler_batch* b) {
 }
 
 int euler_net_batch_simulate(euler_net* const* nets, const euler_run* runs, int32_t count,
-                             int64_t* const* stats, void* cuda_stream) {
+                             int64_t* const* stats, void* cuda_stream) try {
   euler_batch* b = nullptr;
   int rc = euler_batch_create(&b, nets, runs, count);
   if (rc) return rc;
@@ -388,6 +401,10 @@ int euler_net_batch_simulate(euler_net* const* nets, const euler_run* runs, int3
   const int st = euler_batch_status(b, cuda_stream);
   euler_batch_destroy(b);
   return rc ? rc : st;
+} catch (const std::bad_alloc&) {
+  return bfail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return bfail(EULER_ERR_CUDA, "unexpected error");
 }
 
 }  // extern "C"

@@ -30,6 +30,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <new>
 
 #include <cuda_runtime.h>
 
@@ -223,7 +224,7 @@ using namespace eulernet;
 
 extern "C" int euler_net_sojourn(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
                                  uint64_t seed, int64_t rep_begin, int32_t station, int64_t tau0,
-                                 int32_t samples, int32_t* sojourn, int64_t* stats, void* stream) {
+                                 int32_t samples, int32_t* sojourn, int64_t* stats, void* stream) try {
   if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
   if (scheme != EULER_BACKWARD && scheme != EULER_FORWARD) return fail(EULER_ERR_ARG, "unknown scheme");
   if (!(dt > 0.0) || !(T > 0.0) || !std::isfinite(dt) || !std::isfinite(T))
@@ -353,4 +354,8 @@ extern "C" int euler_net_sojourn(euler_net* h, int32_t scheme, double dt, double
   e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "sojourn kernel launch");
   return EULER_OK;
+} catch (const std::bad_alloc&) {
+  return fail(EULER_ERR_OOM, "host memory allocation failed");
+} catch (...) {
+  return fail(EULER_ERR_CUDA, "unexpected error");
 }
