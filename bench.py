@@ -526,8 +526,12 @@ def main():
             h2d = he.h2d_bytes()
             he.close()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 2 * 8 * Bd.stats_len(n, R)}
+        if world > 1:  # the slowest rank's time, as for the device-timed value
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": world * h2d,
+               "d2h_bytes_per_step": world * 2 * 8 * Bd.stats_len(n, R)}
     plans = {"backward": h.plan(0, R), "forward": h.plan(1, R)}
     L = num_levels(run.net)
     launches = {name: launches_per_call(plans[name], sc, K, L) for sc, name in ((0, "backward"), (1, "forward"))}
@@ -570,7 +574,7 @@ def main():
         "per_scheme": {"backward": {"ms_per_launch": kern_ms[0], "value": units_launch / (kern_ms[0] / 1e3)},
                        "forward": {"ms_per_launch": kern_ms[1], "value": units_launch / (kern_ms[1] / 1e3)}},
         "roofline": roof, "cpu_baseline": base, "e2e": e2e, "clocks": clk,
-        "gpu_launches": (launches["backward"] + launches["forward"]) * args.steps,
+        "gpu_launches": (launches["backward"] + launches["forward"]) * args.steps * world,
         "plan": plans,
     }
     print(json.dumps(line), flush=True)
