@@ -89,6 +89,14 @@ static void stream_init(stream_t* s, uint64_t seed, uint32_t purpose, uint32_t s
   s->blk = 0;
 }
 
+/* The stream of another purpose at the same (station, step, replication). */
+static void stream_sibling(stream_t* s, const stream_t* of, uint32_t purpose) {
+  *s = *of;
+  s->ctr[0] = purpose << 24;
+  s->used = 4;
+  s->blk = 0;
+}
+
 static uint32_t next_word(stream_t* s) {
   if (s->used == 4) {
     uint32_t c[4] = {s->ctr[0] | s->blk, s->ctr[1], s->ctr[2], s->ctr[3]};
@@ -482,7 +490,10 @@ static int32_t departure(int32_t x, int32_t m, float mu, float h, float p0, floa
     return k;
   }
   float rate = (float)m * mu;
-  float T = sample_erlang(x - m, rate, st, err);
+  /* T from the Erlang stream (purpose 2) of this station, step and replication */
+  stream_t es;
+  stream_sibling(&es, st, 2u);
+  float T = sample_erlang(x - m, rate, &es, err);
   /* d/dmu log of the Erlang(x - m, m mu) density at T:  (x - m)/mu - m T */
   float te = (float)(x - m) / mu - (float)m * T;
   if (T > h) {
@@ -850,7 +861,7 @@ int eo_draw_poisson(float lam, uint64_t seed, int64_t count, int32_t* out) {
   int err = 0;
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
-    stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
+    stream_init(&st, seed, 1u, 0u, 0u, (uint32_t)j);
     out[j] = sample_poisson(lam, &st, &err);
   }
   return err;
@@ -861,7 +872,7 @@ int eo_draw_binomial(int32_t n, float p, uint64_t seed, int64_t count, int32_t* 
   int err = 0;
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
-    stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
+    stream_init(&st, seed, 1u, 0u, 0u, (uint32_t)j);
     out[j] = sample_binomial(n, p, &st, &err);
   }
   return err;
@@ -872,7 +883,7 @@ int eo_draw_gamma(int32_t k, float rate, uint64_t seed, int64_t count, float* ou
   int err = 0;
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
-    stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
+    stream_init(&st, seed, 1u, 0u, 0u, (uint32_t)j);
     out[j] = sample_erlang(k, rate, &st, &err);
   }
   return err;
@@ -882,7 +893,7 @@ int eo_draw_normal(uint64_t seed, int64_t count, float* out) {
   int err = 0;
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
-    stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
+    stream_init(&st, seed, 1u, 0u, 0u, (uint32_t)j);
     out[j] = sample_normal(&st, &err);
   }
   return err;
@@ -897,7 +908,7 @@ int eo_draw_departure(int32_t x, int32_t m, double mu, double h, uint64_t seed, 
   int err = 0;
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
-    stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
+    stream_init(&st, seed, 1u, 0u, 0u, (uint32_t)j);
     out[j] = departure(x, m, mu_f, h_f, p0, (float)(mu * h), &st, &err, NULL);
   }
   return err;
@@ -921,7 +932,7 @@ int eo_draw_route(int32_t D, int32_t deg, const double* prob, uint64_t seed, int
   int err = 0;
   for (int64_t j = 0; j < count; ++j) {
     stream_t st;
-    stream_init(&st, seed, 2u, 0u, 0u, (uint32_t)j);
+    stream_init(&st, seed, 1u, 0u, 0u, (uint32_t)j);
     int32_t ex = route(D, 0, deg, qc, Redge, &st, &err);
     for (int32_t e = 0; e < deg; ++e) out[j * (deg + 1) + e] = Redge[e];
     out[j * (deg + 1) + deg] = ex;

@@ -124,8 +124,9 @@ float eo_expm1f(float x);
 float eo_log1pf(float x);
 void eo_map_f32(int32_t fn, const float* x, float* y, int64_t count);
 
-/* Draw `count` variates; variate j uses the stream keyed by (seed,
- * purpose 2, station 0, step 0, replication j).  Returns EO_OK or an error. */
+/* Draw `count` variates; variate j uses the service stream keyed by (seed,
+ * purpose 1, station 0, step 0, replication j) (a departure's Erlang time the
+ * purpose-2 stream of the same counter).  Returns EO_OK or an error. */
 int eo_draw_poisson(float lam, uint64_t seed, int64_t count, int32_t* out);
 int eo_draw_binomial(int32_t n, float p, uint64_t seed, int64_t count, int32_t* out);
 int eo_draw_gamma(int32_t k, float rate, uint64_t seed, int64_t count, float* out);

@@ -9,7 +9,8 @@
 //   stream   Philox4x32-10, key = (seed lo, seed hi), counter =
 //            (purpose << 24 | block, station, step, replication); purpose 0 =
 //            external arrivals, 1 = service (departure, then routing edges in
-//            CSR order); words consumed in order.
+//            CSR order), 2 = the Erlang time of a departure draw with x > m;
+//            words consumed in order.
 //   uniform  u = (2 (w >> 9) + 1) 2^-24, exact, in [2^-24, 1 - 2^-24].
 //   exp/log/expm1/log1p  argument reduction + truncated Taylor/atanh series.
 //   Poisson  inversion for lambda < 10, PTRS (Hoermann 1993) otherwise.
@@ -179,6 +180,13 @@ struct PhiloxStream {
   uint32_t w0, w1, w2, w3;          // buffered words, consumed w0 first
   uint32_t left;                    // words remaining in the buffer
   uint32_t block;                   // next block index
+
+  // The stream of another purpose at the same (station, step, replication).
+  EN_D PhiloxStream sibling(uint32_t purpose) const {
+    PhiloxStream s;
+    s.init(key0, key1, purpose, ctr1, ctr2, ctr3);
+    return s;
+  }
 
   EN_D void init(uint32_t k0, uint32_t k1, uint32_t purpose, uint32_t station, uint32_t step,
                  uint32_t rep) {
@@ -501,8 +509,11 @@ EN_COLD float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
 //   x <= m        : Bin(x, p0),                       p0 = 1 - e^{-mu h}
 //   x > m, T > h  : Bin(x - m - 1, h / T)
 //   x > m, T <= h : (x - m) + Bin(m, 1 - e^{-mu (h - T)})
-// Callers draw that binomial next from the same stream, so the draws are
-// exactly Algorithm 1's; lanes on either branch meet again at one binomial.
+// T comes from the unit's Erlang stream (purpose 2), the binomial from the
+// service stream; callers draw that binomial next, so the draws are exactly
+// Algorithm 1's, and lanes on either branch meet again at one binomial.
+// With its own stream the Erlang time's groups of four uniforms are whole
+// Philox blocks, so the lanes that draw one compute each block together.
 struct BinomialArgs {
   int32_t n;
   BinomConst c;
@@ -526,19 +537,23 @@ EN_D BinomialArgs departure_branch(int32_t x, int32_t m, float mu, float h, cons
     return b;
   }
   const float rate = (float)m * mu;
-  const float T = erlang(x - m, rate, st, cx);
+  PhiloxStream es = st.sibling(2u);
+  es.refill();  // every Erlang draw takes at least one word
+  const float T = erlang(x - m, rate, es, cx);
   b.T = T;
+  float pb;
   if (T > h) {
     b.n = x - m - 1;
-    b.c = binom_const(h / T);
+    pb = h / T;
     b.branch = 1;
   } else {
     b.n = m;
     b.p = -fm::expm1(-(mu * (h - T)));
-    b.c = binom_const(b.p);
+    pb = b.p;
     b.base = x - m;
     b.branch = 2;
   }
+  b.c = binom_const(pb);  // one copy for both branches
   return b;
 }
 

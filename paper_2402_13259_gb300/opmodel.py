@@ -28,6 +28,10 @@ STIRLING_SERIES = 6
 BD0_SERIES = 6 + 5 * 3                # setup (sub, abs, add, mul, compare, div...), 5 terms
 LOGPMF_POIS = 2 + LOG + 2 + STIRLING_SERIES + BD0_SERIES
 LOGPMF_BINOM = 3 * STIRLING_SERIES + 2 * BD0_SERIES + 2 * LOG + LOG1P + 8
+# constants of a binomial's p (symmetry test and flip, q = 1 - p, r = p/q,
+# ln(1 - p)): per draw only where p varies (Algorithm 1's x > m branches); the
+# per-station p0 and the per-edge routing probabilities have them precomputed
+BINOM_CONST = 6 + LOG1P
 
 COST: Dict[str, float] = {
     # per event counted by the oracle's work counters
@@ -38,7 +42,7 @@ COST: Dict[str, float] = {
     "pois_ptrs": 14,                   # sqrt, 6 mul/add, 2 div, 2 sub
     "pois_ptrs_iters": 14,             # 2 sub, abs, div, 2 fma-like, floor, 4 compares
     "pois_ptrs_logtests": LOG + 5 + LOGPMF_POIS,
-    "bin_inv": LOG1P + EXP + 8,
+    "bin_inv": EXP + 8,                # (1 - p)^n = exp(n ln(1 - p)), F, u, loop set-up
     "bin_inv_iters": 7,
     "bin_btrs": 20 + LOGPMF_BINOM,
     "bin_btrs_iters": 14,
@@ -49,8 +53,8 @@ COST: Dict[str, float] = {
     "gamma_mt_iters": 14 + 0.05 * (2 * LOG + 8),  # squeeze accepts ~95 %
     "normal_iters": 8 + 0.785 * (LOG + 4),
     "dep_le_m": 2,
-    "dep_t_gt_h": 4,
-    "dep_t_le_h": 6 + EXPM1,
+    "dep_t_gt_h": 4 + BINOM_CONST,
+    "dep_t_le_h": 6 + EXPM1 + BINOM_CONST,
     "route_binomials": 3,
     "gather_edges": 2,
     "units": 24,                       # stream keys, state update, overflow test, 5 statistics
