@@ -147,11 +147,16 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
                                                            int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
   __shared__ float rinv_s[8 * 64];
+  // Let the next slot's CTAs be scheduled as this grid's CTAs finish; they
+  // wait (below) for this grid's completion before reading any state.  In a
+  // launch without programmatic serialisation both are no-ops.
+  asm volatile("griddepcontrol.launch_dependents;");
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* rinv = rinv_s + 64 * wib;
-  for (int k = lane; k < 64; k += 32) rinv[k] = k ? 1.0f / (float)k : 0.0f;
+  for (int k = lane; k < 64; k += 32) rinv[k] = kRinvTable[k];
   __syncwarp();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int32_t slot = *hs.tau + koff;
   if (slot > (phase == 3 ? p.K + t.L - 1 : phase == 4 ? p.K + 1 : p.K)) return;  // uniform
   const int64_t rloc = (int64_t)blockIdx.x * kHbmTile + lane;

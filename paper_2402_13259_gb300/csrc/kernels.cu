@@ -376,20 +376,28 @@ cudaError_t launch_hbm_step(const NetTables& t, const RunParams& p, const HbmSta
 }
 
 namespace {
+// Slot kernels are launched with programmatic stream serialisation: a slot's
+// CTAs may start (and fill their 1/k tables) while the previous slot's last
+// CTAs finish; each waits for the previous grid's completion and memory
+// (griddepcontrol.wait) before it reads the state.
 template <bool GRAD, bool SOJ>
-void launch_slot_kernel(const NetTables& t, const RunParams& p, const HbmState& hs, dim3 grid,
-                        int block, int32_t koff, bool ext, cudaStream_t s) {
-  if (p.scheme == 0) {
-    if (ext)
-      hbm_phase_kernel<4, true, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-    else
-      hbm_phase_kernel<4, false, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-  } else {
-    if (ext)
-      hbm_phase_kernel<3, true, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-    else
-      hbm_phase_kernel<3, false, GRAD, SOJ><<<grid, block, 0, s>>>(t, p, hs, 0, t.n, koff);
-  }
+cudaError_t launch_slot_kernel(const NetTables& t, const RunParams& p, const HbmState& hs, dim3 grid,
+                               int block, int32_t koff, bool ext, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int32_t s0 = 0, m = t.n;
+  if (p.scheme == 0)
+    return ext ? cudaLaunchKernelEx(&cfg, hbm_phase_kernel<4, true, GRAD, SOJ>, t, p, hs, s0, m, koff)
+               : cudaLaunchKernelEx(&cfg, hbm_phase_kernel<4, false, GRAD, SOJ>, t, p, hs, s0, m, koff);
+  return ext ? cudaLaunchKernelEx(&cfg, hbm_phase_kernel<3, true, GRAD, SOJ>, t, p, hs, s0, m, koff)
+             : cudaLaunchKernelEx(&cfg, hbm_phase_kernel<3, false, GRAD, SOJ>, t, p, hs, s0, m, koff);
 }
 
 __global__ void hbm_sojourn_init_kernel(RunParams p, HbmState hs, int32_t station, int32_t tau0) {
@@ -436,13 +444,9 @@ cudaError_t launch_hbm_slot(const NetTables& t, const RunParams& p, const HbmSta
   const unsigned tiles = (unsigned)((p.R + kHbmTile - 1) / kHbmTile);
   dim3 grid(tiles, (unsigned)((t.n + G - 1) / G));
   const bool ext = p.mtab != nullptr || p.dep_mode != 0;
-  if (mode == kHbmGrad)
-    launch_slot_kernel<true, false>(t, p, hs, grid, block, koff, ext, s);
-  else if (mode == kHbmSojourn)
-    launch_slot_kernel<false, true>(t, p, hs, grid, block, koff, ext, s);
-  else
-    launch_slot_kernel<false, false>(t, p, hs, grid, block, koff, ext, s);
-  return cudaGetLastError();
+  if (mode == kHbmGrad) return launch_slot_kernel<true, false>(t, p, hs, grid, block, koff, ext, s);
+  if (mode == kHbmSojourn) return launch_slot_kernel<false, true>(t, p, hs, grid, block, koff, ext, s);
+  return launch_slot_kernel<false, false>(t, p, hs, grid, block, koff, ext, s);
 }
 
 cudaError_t launch_hbm_sojourn_init(const RunParams& p, const HbmState& hs, int32_t station,

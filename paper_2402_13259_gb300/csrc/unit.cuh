@@ -87,8 +87,9 @@ struct UnitOut {
 };
 
 // Departure then routing from input count y (Algorithm 1, then the Sec. 2.2
-// multinomial as sequential conditional binomials), all from the unit's
-// service stream.  One binomial call site serves the departure and every
+// multinomial as sequential conditional binomials), from the unit's service
+// stream (Algorithm 1's Erlang time from its own stream, see
+// departure_branch).  One binomial call site serves the departure and every
 // routing edge, so lanes that took different branches of Algorithm 1 execute
 // the binomial together.
 // EXT: the run may use a staffing schedule or the Eq. (1)/(2) samplers.
@@ -206,8 +207,21 @@ __device__ __forceinline__ int32_t backward_gather(const NetTables& t, int32_t i
   return (int32_t)nn;
 }
 
+// 1/k for k < 64 (entry 0 unused), each the correctly rounded quotient: the
+// compiler folds the constant divisions.
+__device__ const float kRinvTable[64] = {
+    0.0f, 1.0f / 1.0f, 1.0f / 2.0f, 1.0f / 3.0f, 1.0f / 4.0f, 1.0f / 5.0f, 1.0f / 6.0f, 1.0f / 7.0f,
+    1.0f / 8.0f, 1.0f / 9.0f, 1.0f / 10.0f, 1.0f / 11.0f, 1.0f / 12.0f, 1.0f / 13.0f, 1.0f / 14.0f, 1.0f / 15.0f,
+    1.0f / 16.0f, 1.0f / 17.0f, 1.0f / 18.0f, 1.0f / 19.0f, 1.0f / 20.0f, 1.0f / 21.0f, 1.0f / 22.0f, 1.0f / 23.0f,
+    1.0f / 24.0f, 1.0f / 25.0f, 1.0f / 26.0f, 1.0f / 27.0f, 1.0f / 28.0f, 1.0f / 29.0f, 1.0f / 30.0f, 1.0f / 31.0f,
+    1.0f / 32.0f, 1.0f / 33.0f, 1.0f / 34.0f, 1.0f / 35.0f, 1.0f / 36.0f, 1.0f / 37.0f, 1.0f / 38.0f, 1.0f / 39.0f,
+    1.0f / 40.0f, 1.0f / 41.0f, 1.0f / 42.0f, 1.0f / 43.0f, 1.0f / 44.0f, 1.0f / 45.0f, 1.0f / 46.0f, 1.0f / 47.0f,
+    1.0f / 48.0f, 1.0f / 49.0f, 1.0f / 50.0f, 1.0f / 51.0f, 1.0f / 52.0f, 1.0f / 53.0f, 1.0f / 54.0f, 1.0f / 55.0f,
+    1.0f / 56.0f, 1.0f / 57.0f, 1.0f / 58.0f, 1.0f / 59.0f, 1.0f / 60.0f, 1.0f / 61.0f, 1.0f / 62.0f, 1.0f / 63.0f,
+};
+
 __device__ __forceinline__ void fill_rinv(float* rinv) {
-  for (int k = threadIdx.x; k < 64; k += blockDim.x) rinv[k] = k ? 1.0f / (float)k : 0.0f;
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) rinv[k] = kRinvTable[k];
 }
 
 }  // namespace eulernet
