@@ -196,6 +196,58 @@ EULERNET_API int euler_net_grad(euler_net* net, int32_t scheme, double dt, doubl
                                 double* grad, double* value, double* grad_var, double* scores,
                                 int64_t* stats, void* cuda_stream);
 
+/* ---- Checkpoint / resume ---- */
+
+/* Steps step_begin+1 .. K of the run that euler_net_simulate(net, scheme, dt,
+ * T, replications, seed, rep_begin) describes, started from the checkpoint
+ * state_in = N_{step_begin}.  Every draw is keyed by (seed, station, step,
+ * replication), so the counts N after a step are a complete checkpoint: the
+ * statistics of the parts of a run split at any steps add up to those of the
+ * uninterrupted run (the N_K row belongs to the last part), and the last
+ * part's N_K is the same, bit for bit.  (The paper has no checkpointing.)
+ *   step_begin  0 <= step_begin <= K
+ *   state_in    DEVICE [n][replications] int32: N_{step_begin} of station i
+ *               and replication r at i * replications + r; NULL = the
+ *               network's N0 in every replication
+ *   state_out   DEVICE [n][replications] int32 out: N_K; or NULL
+ *   stats       DEVICE stats buffer (the layout of euler_net_simulate), the
+ *               sums over steps step_begin+1 .. K only
+ * Runs in the HBM-state form at any size.  Asynchronous on cuda_stream;
+ * errors as euler_net_simulate, EULER_ERR_ARG for step_begin outside [0, K]. */
+EULERNET_API int euler_net_simulate_resume(euler_net* net, int32_t scheme, double dt, double T,
+                                           int64_t replications, uint64_t seed, int64_t rep_begin,
+                                           int64_t step_begin, const int32_t* state_in,
+                                           int32_t* state_out, int64_t* stats, void* cuda_stream);
+
+/* Coupled gradient: central differences under common random numbers, with
+ * checkpointed replay (an extension; the paper has no gradients).
+ * theta = (mu_0 .. mu_{n-1}, s_0 .. s_{W-1}) where s_w multiplies the external
+ * arrival means Lambda_tau,i of the steps of window w, tau = floor(w K / W) + 1
+ * .. floor((w + 1) K / W), at s = 1.  For parameter c the run is repeated at
+ * theta_c (1 + delta) and theta_c (1 - delta) with the same seed, so both use
+ * the same draws and their sample paths stay coupled; per replication
+ * d_m = (L_m^+ - L_m^-) / (2 delta theta_c), with L_1 = dt sum N and
+ * L_2 = sum D over stations and steps (the measures of euler_net_grad).  A
+ * window perturbation leaves every step before the window unchanged, so its
+ * two runs replay from the base run's checkpoint at the window's first step
+ * (one base pass writes the W - 1 checkpoints into [W-1][n][R] int32 of
+ * device scratch).
+ *   windows   W, 1 <= W <= K
+ *   delta     relative perturbation, 0 < delta <= 1/2
+ *   params    HOST [n_params] indices into theta, or NULL for all n + W
+ *             (n_params must then be n + W)
+ *   grad      DEVICE [2][n_params] double out: mean over replications of d_m
+ *   grad_var  DEVICE [2][n_params] double out: variance of that mean, or NULL
+ * d is summed in int64 (exact), d^2 in double in a fixed order.  Synchronous:
+ * returns when grad and grad_var are written; device-side sampler errors are
+ * latched as for euler_net_simulate.  EULER_ERR_ARG for replications < 1,
+ * W outside [1, K], delta outside (0, 1/2] or an index out of range. */
+EULERNET_API int euler_net_grad_coupled(euler_net* net, int32_t scheme, double dt, double T,
+                                        int64_t replications, uint64_t seed, int64_t rep_begin,
+                                        int32_t windows, double delta, const int32_t* params,
+                                        int32_t n_params, double* grad, double* grad_var,
+                                        void* cuda_stream);
+
 /* ---- Sojourn times (Sec. 6, Algorithm 4) ---- */
 
 /* Sojourn times of tagged customers that enter `station` during step tau0

@@ -32,6 +32,15 @@ static int32_t g_grad_center = 0;  /* eo_grad: 1 = centred estimator */
 int32_t eo_set_grad_center(int32_t on) { int32_t o = g_grad_center; g_grad_center = on ? 1 : 0; return o; }
 
 static int32_t g_dep_mode = 0;  /* 0 exact, 1 Eq. (1), 2 Eq. (2) */
+/* external arrival means of steps lo..hi multiplied by factor (a perturbation
+   of the arrival-rate profile for the coupled gradient; off by default) */
+static int64_t g_win_lo = 1, g_win_hi = 0;
+static double g_win_factor = 1.0;
+void eo_set_arrival_window(int64_t lo, int64_t hi, double factor) {
+  g_win_lo = lo;
+  g_win_hi = hi;
+  g_win_factor = factor;
+}
 int32_t eo_set_departure_mode(int32_t mode) {
   int32_t o = g_dep_mode;
   g_dep_mode = (mode >= 0 && mode <= 2) ? mode : 0;
@@ -685,7 +694,8 @@ static int validate(const eo_net* net) {
  * those stations in index order. */
 static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T, int64_t R,
                          uint64_t seed, int64_t rep_begin, int64_t* stats, int32_t* trace_N,
-                         int32_t* trace_D, int32_t* trace_A, int32_t* trace_R, double* scores) {
+                         int32_t* trace_D, int32_t* trace_A, int32_t* trace_R, double* scores,
+                         int64_t tau0, const int32_t* N_in, int32_t* N_out) {
   int rc = validate(net);
   if (rc) return rc;
   if (!(dt > 0.0) || !(T > 0.0) || R < 0 || rep_begin < 0 || !stats) return EO_ERR_ARG;
@@ -694,6 +704,7 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
   const int32_t n = net->n;
   const int32_t E = net->row_ptr[n];
   const int64_t K = eo_num_steps(dt, T);
+  if (tau0 < 0 || tau0 > K) return EO_ERR_ARG;
 
   int32_t* order = (int32_t*)malloc((size_t)n * sizeof(int32_t));
   rc = topo_order(net, order);
@@ -728,10 +739,15 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
     free(fill);
   }
 
-  /* Lambda table, double -> float, [K][n] */
+  /* Lambda table, double -> float, [K][n]; steps of the perturbation window
+     (eo_set_arrival_window) scaled in double before the rounding */
   float* lam = (float*)malloc((size_t)K * (size_t)n * sizeof(float));
   for (int64_t tau = 1; tau <= K; ++tau)
-    for (int32_t i = 0; i < n; ++i) lam[(tau - 1) * n + i] = (float)interval_rate(net, i, tau, dt);
+    for (int32_t i = 0; i < n; ++i) {
+      double L = interval_rate(net, i, tau, dt);
+      if (tau >= g_win_lo && tau <= g_win_hi) L = L * g_win_factor;
+      lam[(tau - 1) * n + i] = (float)L;
+    }
 
   float* dlam = NULL;           /* [K][n][3] */
   double* mu_acc = NULL;        /* [n] */
@@ -762,13 +778,13 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
   int err = 0;
   for (int64_t r = 0; r < R && !err; ++r) {
     const uint32_t rep = (uint32_t)(rep_begin + r);
-    for (int32_t i = 0; i < n; ++i) N[i] = net->N0 ? net->N0[i] : 0;
+    for (int32_t i = 0; i < n; ++i) N[i] = N_in ? N_in[(int64_t)i * R + r] : net->N0 ? net->N0[i] : 0;
     if (scores)
       for (int32_t i = 0; i < n; ++i) {
         mu_acc[i] = 0.0;
         th_acc[3 * i] = th_acc[3 * i + 1] = th_acc[3 * i + 2] = 0.0;
       }
-    for (int64_t tau = 1; tau <= K && !err; ++tau) {
+    for (int64_t tau = tau0 + 1; tau <= K && !err; ++tau) {
       const float* lam_t = lam + (tau - 1) * n;
       const int32_t* m_t = servers_of_step(net, tau, dt);
       if (scheme == EO_BACKWARD) {
@@ -838,6 +854,8 @@ static int simulate_impl(const eo_net* net, int32_t scheme, double dt, double T,
         for (int32_t e = 0; e < E; ++e) trace_R[((tau - 1) * E + e) * R + r] = Redge[e];
     }
     for (int32_t i = 0; i < n; ++i) st_NK[i] += N[i];
+    if (N_out)
+      for (int32_t i = 0; i < n; ++i) N_out[(int64_t)i * R + r] = N[i];
     if (scores) {
       double* sr = scores + r * (int64_t)(n + 3);
       for (int32_t i = 0; i < n; ++i) sr[i] = mu_acc[i];
@@ -952,7 +970,18 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T, int64_t 
                 int64_t rep_begin, int64_t* stats, int32_t* trace_N, int32_t* trace_D,
                 int32_t* trace_A) {
   return simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, trace_N, trace_D, trace_A,
-                       NULL, NULL);
+                       NULL, NULL, 0, NULL, NULL);
+}
+
+/* Checkpoint / resume: the steps tau0+1..K from the state N_in = N_tau0
+ * ([n][R], replication fastest; NULL = N0 of the network), keyed exactly as
+ * in the uninterrupted run, so the two halves of a split run reproduce it.
+ * N_out ([n][R] or NULL) receives N_K. */
+int eo_simulate_resume(const eo_net* net, int32_t scheme, double dt, double T, int64_t R,
+                       uint64_t seed, int64_t rep_begin, int64_t tau0, const int32_t* N_in,
+                       int32_t* N_out, int64_t* stats) {
+  return simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, NULL, NULL, NULL, NULL, NULL,
+                       tau0, N_in, N_out);
 }
 
 /* Likelihood-ratio (score-function) gradient of the two measures
@@ -970,7 +999,8 @@ int eo_grad(const eo_net* net, int32_t scheme, double dt, double T, int64_t R, u
   const int64_t C = n + 3;
   int64_t* stats = (int64_t*)malloc((size_t)(6 * (int64_t)n + 4 * R) * sizeof(int64_t));
   double* sc = scores_out ? scores_out : (double*)malloc((size_t)(R * C) * sizeof(double));
-  int rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, NULL, NULL, NULL, NULL, sc);
+  int rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, stats, NULL, NULL, NULL, NULL, sc,
+                         0, NULL, NULL);
   if (rc == EO_OK) {
     const int64_t* rp = stats + 5 * (int64_t)n;
     for (int m = 0; m < 2; ++m) {
@@ -1081,7 +1111,8 @@ int eo_sojourn(const eo_net* net, int32_t scheme, double dt, double T, int64_t R
     free(tN); free(tD); free(tR); if (!stats) free(st);
     return EO_ERR_ARG;
   }
-  rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, st, tN, tD, NULL, tR, NULL);
+  rc = simulate_impl(net, scheme, dt, T, R, seed, rep_begin, st, tN, tD, NULL, tR, NULL, 0, NULL,
+                     NULL);
   /* path values: step tau in 1..K, station i, replication r */
 #define PN(tau, i) tN[(((tau) - 1) * n + (i)) * R + r]
 #define PD(tau, i) tD[(((tau) - 1) * n + (i)) * R + r]

@@ -84,6 +84,18 @@ int eo_simulate(const eo_net* net, int32_t scheme, double dt, double T,
                 int64_t R, uint64_t seed, int64_t rep_begin, int64_t* stats,
                 int32_t* trace_N, int32_t* trace_D, int32_t* trace_A);
 
+/* Checkpoint / resume: steps tau0+1..K from N_in = N_tau0 ([n][R],
+ * replication fastest; NULL = N0), statistics over those steps only (the
+ * layout of eo_simulate), N_K into N_out ([n][R] or NULL). */
+int eo_simulate_resume(const eo_net* net, int32_t scheme, double dt, double T, int64_t R,
+                       uint64_t seed, int64_t rep_begin, int64_t tau0, const int32_t* N_in,
+                       int32_t* N_out, int64_t* stats);
+
+/* Multiply the external arrival means Lambda_tau,i of steps lo..hi by
+ * `factor` (in double, before the rounding to float) in later runs;
+ * (1, 0, 1.0) switches it off. */
+void eo_set_arrival_window(int64_t lo, int64_t hi, double factor);
+
 /* Likelihood-ratio gradient of L1 = dt sum N and L2 = sum D with respect to
  * (mu_1..mu_n, a, b, phase) of the sinusoid arrivals (centred with
  * eo_set_grad_center(1)); see euler_oracle.c.

@@ -6,6 +6,7 @@ off, so every float expression is evaluated exactly as written.
 """
 from __future__ import annotations
 
+import copy
 import ctypes as C
 import os
 import subprocess
@@ -108,6 +109,11 @@ def lib():
         L.eo_sojourn_pstay.restype = C.c_float
         L.eo_grad.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
                               C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.eo_simulate_resume.restype = C.c_int
+        L.eo_simulate_resume.argtypes = [C.POINTER(_Net), C.c_int32, C.c_double, C.c_double, C.c_int64,
+                                         C.c_uint64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        L.eo_set_arrival_window.argtypes = [C.c_int64, C.c_int64, C.c_double]
         _lib = L
     return _lib
 
@@ -264,6 +270,86 @@ def des_sojourn(net: Network, dt: float, T: float, R: int, seed: int, station: i
 def sojourn_pstay(x: int, d: int, m: int) -> float:
     """Lemma 3's stay probability as the oracle evaluates it (float32)."""
     return float(lib().eo_sojourn_pstay(int(x), int(d), int(m)))
+
+
+def simulate_resume(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, tau0: int,
+                    N_in: Optional[np.ndarray] = None, rep_begin: int = 0):
+    """Steps tau0+1 .. K from N_in ([n, R] int32, N_tau0; None = N0), see
+    eo_simulate_resume: dict with the statistics of those steps (as
+    simulate()) and 'N_out' [n, R], N_K."""
+    L = lib()
+    s, keep = _make_net(net)
+    n = net.n
+    stats = np.zeros(6 * n + 4 * R, dtype=np.int64)
+    nin = None if N_in is None else np.ascontiguousarray(N_in, dtype=np.int32).reshape(n, R)
+    nout = np.zeros((n, R), dtype=np.int32)
+    rc = L.eo_simulate_resume(C.byref(s), scheme, dt, T, R, seed, rep_begin, tau0, _ptr(nin),
+                              _ptr(nout), _ptr(stats))
+    del keep
+    if rc != 0:
+        raise RuntimeError(f"oracle eo_simulate_resume failed with code {rc}")
+    out = {"stats": stats, "N_out": nout}
+    out.update(stats_split(stats, n, R))
+    return out
+
+
+def set_arrival_window(lo: int, hi: int, factor: float):
+    """Multiply the external arrival means of steps lo..hi by `factor` in
+    later runs; set_arrival_window(1, 0, 1.0) switches it off."""
+    lib().eo_set_arrival_window(lo, hi, factor)
+
+
+def grad_coupled(net: Network, scheme: int, dt: float, T: float, R: int, seed: int, windows: int,
+                 delta: float, params=None, rep_begin: int = 0):
+    """Central differences under common random numbers of L_1 = dt sum N and
+    L_2 = sum D with respect to theta = (mu_0..mu_{n-1}, s_0..s_{W-1}), s_w a
+    factor on the external arrival means of the steps of window w, steps
+    floor(wK/W)+1 .. floor((w+1)K/W).  Parameter c: the run at
+    theta_c (1 + delta) minus the run at theta_c (1 - delta), same seed, per
+    replication, over 2 delta theta_c; a window's runs start from N at the
+    step before the window (itself from a run of the unperturbed network).
+    Returns 'grad' and 'var' (variance of the mean), [2, len(params)]: the
+    mean from the exact integer sum of the differences, the variance from
+    S2 = sum of squares in ascending replication order."""
+    n = net.n
+    K = num_steps(dt, T)
+    P = n + windows
+    idx = list(range(P)) if params is None else [int(c) for c in params]
+    g = np.zeros((2, len(idx)))
+    var = np.zeros((2, len(idx)))
+    for k, c in enumerate(idx):
+        if c < n:
+            theta = float(net.mu[c])
+            runs = []
+            for f in (1.0 + delta, 1.0 - delta):
+                pert = copy.deepcopy(net)
+                pert.mu = np.array(net.mu, dtype=np.float64)
+                pert.mu[c] = theta * f
+                runs.append(simulate_resume(pert, scheme, dt, T, R, seed, 0, None, rep_begin))
+        else:
+            theta = 1.0
+            w = c - n
+            lo, hi = w * K // windows + 1, (w + 1) * K // windows
+            start = None
+            if lo > 1:
+                start = simulate_resume(net, scheme, dt, (lo - 1) * dt, R, seed, 0, None, rep_begin)["N_out"]
+            runs = []
+            for f in (1.0 + delta, 1.0 - delta):
+                set_arrival_window(lo, hi, f)
+                try:
+                    runs.append(simulate_resume(net, scheme, dt, T, R, seed, lo - 1, start, rep_begin))
+                finally:
+                    set_arrival_window(1, 0, 1.0)
+        for m in range(2):
+            d = runs[0]["rep"][:, m] - runs[1]["rep"][:, m]  # int64, Q_r (m = 0) or D_r (m = 1)
+            S1 = float(int(d.sum()))
+            S2 = 0.0
+            for x in d.tolist():
+                S2 += float(x) * float(x)
+            scale = (dt if m == 0 else 1.0) / (2.0 * delta * theta)
+            g[m, k] = (S1 / R) * scale
+            var[m, k] = ((S2 - S1 * (S1 / R)) / (R - 1)) * (scale * scale) / R if R > 1 else 0.0
+    return {"grad": g, "var": var}
 
 
 def set_grad_center(on: bool) -> int:

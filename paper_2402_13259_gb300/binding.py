@@ -91,6 +91,9 @@ def lib():
         L.euler_net_grad.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, vp, vp, vp, vp, vp, vp]
         L.euler_net_grad.restype = C.c_int
         L.euler_net_sojourn.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, i32, i64, i32, vp, vp, vp]
+        L.euler_net_simulate_resume.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, i64, vp, vp, vp, vp]
+        L.euler_net_grad_coupled.argtypes = [vp, i32, dbl, dbl, i64, u64, i64, i32, dbl, vp, i32, vp,
+                                             vp, vp]
         L.euler_net_sojourn.restype = C.c_int
         L.euler_net_simulate_average.argtypes = [vp, dbl, dbl, i64, u64, i64, vp, vp, vp, vp]
         L.euler_net_simulate_average.restype = C.c_int
@@ -256,6 +259,47 @@ class EulerNet:
         _check(lib().euler_net_grad(self._h, scheme, dt, T, R, seed, rep_begin, ptr("grad"), ptr("value"),
                                     ptr("var"), ptr("scores"), ptr("stats"),
                                     C.c_void_p(_stream_ptr(stream))))
+        if check:
+            self.status(stream)
+        return out
+
+    def simulate_resume(self, scheme: int, dt: float, T: float, R: int, seed: int, step_begin: int,
+                        state_in=None, state_out: bool = False, rep_begin: int = 0, stats=None,
+                        stream=None, check: bool = True):
+        """Steps step_begin+1 .. K from the checkpoint state_in (int32 device
+        tensor [n, R] of N_{step_begin}, or None for N0), see
+        euler_net_simulate_resume: returns (stats, N_K [n, R] or None)."""
+        import torch
+        n = self.n
+        if stats is None:
+            stats = torch.empty(stats_len(n, R), dtype=torch.int64, device="cuda")
+        out = torch.empty((n, R), dtype=torch.int32, device="cuda") if state_out else None
+        if state_in is not None:
+            assert state_in.dtype == torch.int32 and state_in.is_contiguous() and tuple(state_in.shape) == (n, R)
+        _check(lib().euler_net_simulate_resume(
+            self._h, scheme, dt, T, R, seed, rep_begin, step_begin,
+            None if state_in is None else C.c_void_p(state_in.data_ptr()),
+            None if out is None else C.c_void_p(out.data_ptr()), C.c_void_p(stats.data_ptr()),
+            C.c_void_p(_stream_ptr(stream))))
+        if check:
+            self.status(stream)
+        return stats, out
+
+    def grad_coupled(self, scheme: int, dt: float, T: float, R: int, seed: int, windows: int,
+                     delta: float, params=None, rep_begin: int = 0, stream=None, check: bool = True):
+        """Coupled central-difference gradient with checkpointed replay (see
+        euler_net_grad_coupled): dict of device tensors 'grad' and 'var',
+        [2, len(params)] (params default: all n + windows)."""
+        import torch
+        P = self.n + windows
+        idx = None if params is None else np.ascontiguousarray(params, dtype=np.int32)
+        k = P if idx is None else int(idx.size)
+        dev = dict(dtype=torch.float64, device="cuda")
+        out = {"grad": torch.empty((2, k), **dev), "var": torch.empty((2, k), **dev)}
+        _check(lib().euler_net_grad_coupled(self._h, scheme, dt, T, R, seed, rep_begin, windows, delta,
+                                            _ptr(idx), k, C.c_void_p(out["grad"].data_ptr()),
+                                            C.c_void_p(out["var"].data_ptr()),
+                                            C.c_void_p(_stream_ptr(stream))))
         if check:
             self.status(stream)
         return out

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeulernet.so")
-SOURCES = ["kernels.cu", "pipeline.cu", "abi.cu", "noalloc.cu", "batch.cu", "sojourn.cu"]
+SOURCES = ["kernels.cu", "pipeline.cu", "abi.cu", "noalloc.cu", "batch.cu", "sojourn.cu", "coupled.cu"]
 HEADERS = ["sampling.cuh", "internal.h", "handle.h", "unit.cuh", "tile.cuh", "hbm_step.cuh", os.path.join("..", "..", "include", "eulernet.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")

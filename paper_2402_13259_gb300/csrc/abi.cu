@@ -143,7 +143,11 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
   for (int32_t i = 0; i < h->n; ++i) {
     const int32_t c = h->ex_col[i];
     if (c < 0) continue;
-    for (int64_t tau = 1; tau <= K; ++tau) lam[(size_t)(tau - 1) * h->n_ex + c] = (float)step_mean(*h, i, tau, dt);
+    for (int64_t tau = 1; tau <= K; ++tau) {
+      double L = step_mean(*h, i, tau, dt);
+      if (tau >= h->win_lo && tau <= h->win_hi) L = L * h->win_factor;
+      lam[(size_t)(tau - 1) * h->n_ex + c] = (float)L;
+    }
   }
   if (!h->d_p0) CUDA_TRY(cudaMalloc(&h->d_p0, sizeof(float4) * (size_t)h->n));
   if (lam.size() > h->lam_cap) {
@@ -382,16 +386,21 @@ int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p,
   hs.csteps = x.csteps;
   hs.col = x.col;
   hs.S = x.S;
-  // backward: K + 1 fused slots; forward: K + L - 1 skewed slots
-  const int64_t slots = hbm_slots(h, p.scheme, p.K);
+  hs.state_in = x.state_in;
+  hs.state_out = x.state_out;
+  hs.state_ld = p.R;
+  // backward: K + 1 fused slots; forward: K + L - 1 skewed slots (from
+  // slot tau0 + 1 in a resumed run)
+  const int64_t slots = hbm_slots(h, p.scheme, p.K) - p.tau0;
   const int64_t S = h->opt[EULER_OPT_GRAPH_STEPS] > 0 ? h->opt[EULER_OPT_GRAPH_STEPS]
-                                                      : std::min<int64_t>(slots, 32);
+                                                      : std::min<int64_t>(std::max<int64_t>(slots, 1), 32);
   if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   for (int64_t r0 = 0; r0 < p.R; r0 += Rc) {
     RunParams pc = p;
     pc.R = std::min<int64_t>(Rc, p.R - r0);
     pc.rep_begin = p.rep_begin + r0;
     pc.num_tiles = (pc.R + 31) / 32;
+    hs.state_r0 = r0;
     if (x.mode == kHbmGrad) {
       pc.scores = p.scores + r0 * ((int64_t)h->n + 3);
       CUDA_TRY(cudaMemsetAsync(x.mu_acc, 0, sizeof(double) * (size_t)h->n * hs.ld, s));
@@ -415,7 +424,7 @@ int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p,
     cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    const int64_t replays = (slots + S - 1) / S;
+    const int64_t replays = slots > 0 ? (slots + S - 1) / S : 0;
     for (int64_t k = 0; k < replays && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
     cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");

@@ -34,6 +34,11 @@ struct euler_net {
   size_t mtab_cap = 0;
   float* d_muh = nullptr;
 
+  // external arrival means of steps win_lo .. win_hi multiplied by win_factor
+  // (a perturbation of the coupled gradient; off when win_hi < win_lo)
+  int64_t win_lo = 1, win_hi = 0;
+  double win_factor = 1.0;
+
   // per-(dt, T) tables of the last call
   double c_dt = -1.0, c_T = -1.0;
   int32_t c_K = 0;
@@ -123,6 +128,8 @@ struct HbmExtra {
   const int32_t* col = nullptr;
   int32_t S = 0, station = 0, tau0 = 0;
   int32_t* out = nullptr;              // [R][S]
+  const int32_t* state_in = nullptr;   // checkpoint N_{p.tau0}, [n][R], or nullptr (N0)
+  int32_t* state_out = nullptr;        // N_K out, [n][R], or nullptr
 };
 
 // One call in the HBM form: state set-up, the graph of per-step kernels

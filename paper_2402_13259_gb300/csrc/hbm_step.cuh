@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
     int32_t* redge = hs.Redge;
     if (phase == 3) {
       tau = slot - __ldg(hs.pos_level + s0 + su);
-      live = tau >= 1 && tau <= p.K;
+      live = tau > p.tau0 && tau <= p.K;
       if (!live) return;  // uniform across the warp
       redge = hs.Redge + (int64_t)(tau % hs.depth) * t.E * hs.ld;
     }
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
     } else if constexpr (phase == 4) {  // backward, fused: gather tau - 1, then draw tau
       int32_t v[5] = {0, 0, 0, 0, 0};
       if (act) {
-        if (slot >= 2) {
+        if (slot >= p.tau0 + 2) {
           const int32_t* rprev = hs.Redge + (int64_t)((slot - 1) & 1) * t.E * hs.ld;
           const int32_t nn = backward_gather(t, i, hs.N, rprev, hs.ld, rloc, cx.err);
           const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)(slot - 1));
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
                 soj_step<EXT>(t, p, hs, ci, c, i, slot, rep, o.x, o.D, rcur, rloc);
             }
           }
-        } else if (SOJ && slot >= 2) {  // slot K+1: the last setups only
+        } else if (SOJ && slot >= p.tau0 + 2) {  // slot K+1: the last setups only
           for (int32_t c = 0; c < hs.S; ++c) {
             const int64_t ci = (int64_t)c * hs.ld + rloc;
             const unsigned long long w = hs.cloc[ci];

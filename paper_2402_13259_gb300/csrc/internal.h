@@ -53,6 +53,7 @@ struct RunParams {
   double* scores;     // [R][n+3] per-replication scores out
   int64_t* stats;     // output, see eulernet.h
   unsigned* err;      // latched error bits
+  int32_t tau0 = 0;   // the run covers steps tau0+1 .. K (HBM form; a resumed run)
 };
 
 // Shared-memory bytes of the persistent kernel for a tile of `tile_reps`.
@@ -118,6 +119,11 @@ struct HbmState {
   int32_t* csteps = nullptr;           // [S][ld] steps accounted
   const int32_t* col = nullptr;        // [E] destination station of each edge
   int32_t S = 0;
+  // checkpoint / resume: N_tau0 in and N_K out, [n][state_ld] (replication
+  // fastest, this chunk's replications from column state_r0), or nullptr
+  const int32_t* state_in = nullptr;
+  int32_t* state_out = nullptr;
+  int64_t state_ld = 0, state_r0 = 0;
 };
 
 // What the HBM form's per-step kernels compute besides the step.

@@ -189,15 +189,22 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const NetTables* nets, co
 
 __global__ void hbm_advance_kernel(int32_t* tau, int32_t by) { *tau += by; }
 
+// State N_{tau0} (the network's N0, or a checkpoint), per-replication sums
+// zeroed, step counter at the run's first slot tau0 + 1.
 __global__ void hbm_init_kernel(NetTables t, RunParams p, HbmState hs) {
   const int64_t total = (int64_t)t.n * hs.ld;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x)
-    hs.N[k] = t.N0 ? __ldg(t.N0 + k / hs.ld) : 0;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k / hs.ld, r = k - i * hs.ld;
+    if (hs.state_in)
+      hs.N[k] = r < p.R ? hs.state_in[i * hs.state_ld + hs.state_r0 + r] : 0;
+    else
+      hs.N[k] = t.N0 ? __ldg(t.N0 + i) : 0;
+  }
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * p.R;
        k += (int64_t)gridDim.x * blockDim.x)
     hs.racc[k] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *hs.tau = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hs.tau = p.tau0 + 1;
 }
 
 // Per-replication sums out, and N_K summed over replications (one block per
@@ -211,6 +218,9 @@ __global__ void hbm_finish_kernel(NetTables t, RunParams p, HbmState hs, int64_t
     st_rep[k] = hs.racc[k];
   __shared__ long long part[32];
   for (int32_t i = blockIdx.x; i < t.n; i += gridDim.x) {
+    if (hs.state_out)  // the checkpoint N_K of this chunk's replications
+      for (int64_t k = threadIdx.x; k < p.R; k += blockDim.x)
+        hs.state_out[(int64_t)i * hs.state_ld + hs.state_r0 + k] = hs.N[(int64_t)i * hs.ld + k];
     const int4* row = reinterpret_cast<const int4*>(hs.N + (int64_t)i * hs.ld);
     long long s = 0;
     const int64_t nvec = p.R / 4;

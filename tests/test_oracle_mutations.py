@@ -70,6 +70,15 @@ MUTANTS = [
      "if (k <= v) { next = net->col[e]; break; }"),
     # exp: a Taylor coefficient slip
     ("exp_coeff", "p = fmaf(p, r, (float)(1.0 / 6.0));", "p = fmaf(p, r, (float)(1.0 / 7.0));"),
+    # resume: the checkpoint ignored (every part restarts from N0)
+    ("resume_state_ignored", "N[i] = N_in ? N_in[(int64_t)i * R + r] : net->N0 ? net->N0[i] : 0;",
+     "N[i] = net->N0 ? net->N0[i] : 0;"),
+    # resume: the checkpoint's own step run again
+    ("resume_step_offset", "for (int64_t tau = tau0 + 1; tau <= K && !err; ++tau) {",
+     "for (int64_t tau = tau0 > 0 ? tau0 : 1; tau <= K && !err; ++tau) {"),
+    # coupled gradient: the last step of a perturbation window left unscaled
+    ("window_range", "if (tau >= g_win_lo && tau <= g_win_hi) L = L * g_win_factor;",
+     "if (tau >= g_win_lo && tau < g_win_hi) L = L * g_win_factor;"),
 ]
 
 

@@ -835,3 +835,133 @@ def test_sojourn_bookkeeping(orc):
     assert st.max() <= K - 50 and st.min() >= -(K - 50)
     for bad in (dict(station=3, tau0=1), dict(station=0, tau0=0), dict(station=0, tau0=K + 1)):
         assert orc.sojourn(net, 0, dt, 2.0, 4, 5, expect_ok=False, **bad)["rc"] != 0
+
+
+# ---------------------------------------------------------------------------
+# Checkpoint / resume and the coupled gradient
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_resume_reproduces_the_uninterrupted_run(orc, scheme):
+    """Draws are keyed by (seed, station, step, replication): a run split at
+    any steps, each part started from the counts N where the previous one
+    stopped, has the statistics of the whole run (sums add up) and its final
+    counts, bit for bit."""
+    rng = np.random.default_rng(3)
+    net = W.random_small_dag(rng, 6, max_deg=2, m_range=(1, 4), ext_frac=0.5, lam_scale=3.0)
+    net.N0 = np.arange(6, dtype=np.int32) % 3
+    dt, K, R, seed = 0.1, 37, 50, 5
+    full = orc.simulate_resume(net, scheme, dt, K * dt, R, seed, 0)
+    plain = orc.simulate(net, scheme, dt, K * dt, R, seed)
+    assert np.array_equal(full["stats"], plain["stats"])
+    for cuts in ([0, 37], [0, 1, 37], [0, 12, 25, 36, 37]):
+        st, rp, N = np.zeros_like(full["station"]), np.zeros_like(full["rep"]), None
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            part = orc.simulate_resume(net, scheme, dt, b * dt, R, seed, a, N)
+            st += part["station"]
+            rp += part["rep"]
+            N = part["N_out"]
+            assert np.array_equal(part["NK"], N.sum(axis=1))
+        assert np.array_equal(st, full["station"]) and np.array_equal(rp, full["rep"])
+        assert np.array_equal(N, full["N_out"])
+    # a run with no steps left keeps the checkpoint
+    last = orc.simulate_resume(net, scheme, dt, K * dt, R, seed, K, full["N_out"])
+    assert np.array_equal(last["N_out"], full["N_out"]) and not last["station"].any()
+    # the checkpoint is per replication: other counts give another continuation
+    other = orc.simulate_resume(net, scheme, dt, K * dt, R, seed, 12, np.zeros((6, R), np.int32))
+    assert not np.array_equal(other["N_out"], full["N_out"])
+
+
+def _inf_server_measures_scaled(net, scheme, dt, K, scale):
+    """E[L1], E[L2] of the no-queueing recursion with Lambda_tau scaled by scale(tau)."""
+    a = net.arrivals
+    om = 2 * math.pi / a.period
+    stay = np.exp(-net.mu * dt)
+    m = np.zeros(net.n)
+    L1 = L2 = 0.0
+    for tau in range(1, K + 1):
+        t0, t1 = (tau - 1) * dt, tau * dt
+        lam = scale(tau) * a.w * a.a * ((t1 - t0) + a.b * (math.cos(om * t0 + a.phase) - math.cos(om * t1 + a.phase)) / om)
+        if scheme == 0:
+            d = (1 - stay) * m
+            new = m - d + lam
+            for k in range(net.n):
+                for e in range(net.row_ptr[k], net.row_ptr[k + 1]):
+                    new[net.col[e]] += net.prob[e] * d[k]
+            m = new
+        else:
+            y = m + lam
+            d = np.zeros(net.n)
+            for k in range(net.n):
+                d[k] = (1 - stay[k]) * y[k]
+                for e in range(net.row_ptr[k], net.row_ptr[k + 1]):
+                    y[net.col[e]] += net.prob[e] * d[k]
+            m = y - d
+        L1 += dt * m.sum()
+        L2 += d.sum()
+    return np.array([L1, L2])
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_coupled_gradient_infinite_server_closed_form(orc, scheme):
+    """Without queueing E[L] follows exact linear recursions, so the expected
+    central difference of each parameter (mu_i at mu_i (1 +- delta); the
+    arrival means of one time window at (1 +- delta)) is known: the coupled
+    estimator must match it within its confidence interval.  Its window
+    derivatives add up to the derivative for scaling every step, the
+    integral of the response to an arrival over the rest of the horizon."""
+    rng = np.random.default_rng(8)
+    net = W.random_small_dag(rng, 4, max_deg=2, ext_frac=1.0, lam_scale=8.0)
+    net.servers[:] = 1_000_000
+    net.arrivals.a, net.arrivals.b, net.arrivals.phase = 1.0, 0.5, 0.3
+    dt, K, R, W_, delta = 0.1, 30, 4000, 3, 0.05
+    g = orc.grad_coupled(net, scheme, dt, K * dt, R, 23, W_, delta)
+    want = np.zeros((2, net.n + W_))
+    for i in range(net.n):
+        up, dn = net.mu.copy(), net.mu.copy()
+        up[i] *= 1 + delta
+        dn[i] *= 1 - delta
+        want[:, i] = (_inf_server_measures(net, scheme, dt, K, mu=up) -
+                      _inf_server_measures(net, scheme, dt, K, mu=dn)) / (2 * delta * net.mu[i])
+    for w in range(W_):
+        lo, hi = w * K // W_ + 1, (w + 1) * K // W_
+        f = lambda s: (lambda tau: s if lo <= tau <= hi else 1.0)  # noqa: E731
+        want[:, net.n + w] = (_inf_server_measures_scaled(net, scheme, dt, K, f(1 + delta)) -
+                              _inf_server_measures_scaled(net, scheme, dt, K, f(1 - delta))) / (2 * delta)
+    se = np.sqrt(g["var"])
+    z = (g["grad"] - want) / np.maximum(se, 1e-12)
+    assert np.abs(z).max() < 5.0, z
+    # linear in the arrival scale: the windows add up to the whole horizon's
+    whole = (_inf_server_measures_scaled(net, scheme, dt, K, lambda t: 1 + delta) -
+             _inf_server_measures_scaled(net, scheme, dt, K, lambda t: 1 - delta)) / (2 * delta)
+    assert np.allclose(want[:, net.n:].sum(axis=1), whole, rtol=1e-9)
+    # a later window matters less for the time-integrated count (less time left)
+    assert want[0, net.n] > want[0, net.n + 1] > want[0, net.n + 2] > 0
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_coupled_gradient_agrees_with_likelihood_ratio(orc, scheme):
+    """On a queueing tandem where every branch of Algorithm 1 occurs, the
+    coupled central differences in mu_i and the likelihood-ratio gradient
+    estimate the same derivatives (up to the O(delta^2) bias of a central
+    difference).  Common random numbers keep the two runs' paths together:
+    the per-replication spread of the difference quotient is well below
+    that of the same quotient from independent runs,
+    sqrt(2 Var L) / (2 delta mu)."""
+    net = _queueing_net()
+    dt, T, R, Rc, delta = 0.3, 3.0, 40000, 4000, 0.05
+    old = orc.set_grad_center(1)
+    try:
+        lr = orc.grad(net, scheme, dt, T, R, 17)
+    finally:
+        orc.set_grad_center(old)
+    cp = orc.grad_coupled(net, scheme, dt, T, Rc, 17, 2, delta, params=[0, 1])
+    se = np.sqrt(lr["var"][:, :2] + cp["var"])
+    z = (cp["grad"] - lr["grad"][:, :2]) / se
+    assert np.abs(z).max() < 5.0, z
+    base = orc.simulate(net, scheme, dt, T, Rc, 17)
+    L = [dt * base["rep"][:, 0], base["rep"][:, 1]]
+    independent = np.array([[math.sqrt(2 * L[m].var()) / (2 * delta * net.mu[c]) for c in (0, 1)]
+                            for m in (0, 1)])
+    coupled = np.sqrt(cp["var"] * Rc)
+    ratio = coupled / independent
+    assert np.all(ratio < 0.5) and np.median(ratio) < 0.2, ratio
