@@ -301,7 +301,8 @@ def run_rows(args):
     stream (one warm-up call with the same dt and T first): the average
     scheme, sojourn times, a staffing schedule, the Eq. (1)/(2) departure
     samplers, likelihood-ratio gradients (100,000 replications of the
-    sinusoid-arrival DAG) and the staffing-scale sweep (2,000 stations,
+    sinusoid-arrival DAG), the coupled gradient in ten arrival windows with
+    checkpointed replay (10,000 replications) and the staffing-scale sweep (2,000 stations,
     dt = 1/sqrt(s); 100,000 replications for s <= 100, 16,384 above).  One JSON line per row; bit-exact
     parity of each row is in the GPU tests."""
     import numpy as np
@@ -403,6 +404,23 @@ def run_rows(args):
              {"workload": f"dag100 with sinusoid arrivals, R={g.R}, T={g.T:g}, dt={g.dt:g}",
               "gradient": "d/d(mu_1..mu_100, a, b, phase) of dt sum N and sum D"},
              "euler_net_grad", "tests/test_gpu_grad.py")
+    hg.status()
+    # C4, coupled variant: central differences under common random numbers in
+    # the arrival scale of each of 10 time windows, each window's two runs
+    # replayed from the base pass's checkpoint at the window start
+    Wn, Rc = 10, 10000
+    par = list(range(g.net.n, g.net.n + Wn))
+    steps_run = Kg + sum(2 * (Kg - (w * Kg // Wn)) for w in range(Wn))  # base pass + replays
+    steps_full = Kg + 2 * Wn * Kg  # the same without checkpoints
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        ms = timed(lambda: hg.grad_coupled(scheme, g.dt, g.T, Rc, g.seed, Wn, 0.05, params=par, check=False),
+                   lambda: hg.grad_coupled(scheme, g.dt, g.T, 64, g.seed, Wn, 0.05, params=par, check=False))
+        emit(f"c4_coupled_gradient_{name}", g.net.n * steps_run * Rc, ms, None,
+             {"workload": f"dag100 with sinusoid arrivals, R={Rc}, T={g.T:g}, dt={g.dt:g}",
+              "gradient": f"d/d(arrival scale of {Wn} time windows) of dt sum N and sum D, "
+                          "central differences, delta = 0.05, common random numbers",
+              "steps_simulated": steps_run, "steps_without_checkpoints": steps_full},
+             "euler_net_grad_coupled", "tests/test_gpu_resume.py")
     hg.status()
     hg.close()
     # C2: staffing-scale sweep (2,000 stations); the full 100,000 replications
