@@ -47,6 +47,15 @@
 #define EN_REFILL EN_D
 #endif
 
+// Branch-probability hints (code placement only: the arithmetic is the same).
+#if defined(__CUDACC__) || defined(__GNUC__)
+#define EN_LIKELY(c) __builtin_expect(!!(c), 1)
+#define EN_UNLIKELY(c) __builtin_expect(!!(c), 0)
+#else
+#define EN_LIKELY(c) (c)
+#define EN_UNLIKELY(c) (c)
+#endif
+
 namespace eulernet {
 
 // Error bits latched in the handle's device error word.
@@ -92,9 +101,9 @@ EN_HD float qnan() { return bits_f(0x7fc00000u); }
 // e^x = 2^k e^r, k = floor(x log2e + 1/2), r = x - k ln2 in two parts;
 // e^r by its degree-7 Taylor polynomial in Horner form.
 EN_HD float exp(float x) {
-  if (x != x) return x;
-  if (x > 88.72283935546875f) return inf();
-  if (x < -103.97207641601562f) return 0.0f;
+  if (EN_UNLIKELY(x != x)) return x;
+  if (EN_UNLIKELY(x > 88.72283935546875f)) return inf();
+  if (EN_UNLIKELY(x < -103.97207641601562f)) return 0.0f;
   const float k = floorf(x * kLog2e + 0.5f);
   float r = fmaf(-k, kLn2Hi, x);
   r = fmaf(-k, kLn2Lo, r);
@@ -107,20 +116,20 @@ EN_HD float exp(float x) {
   s = fmaf(s, r, 1.0f);
   s = fmaf(s, r, 1.0f);
   const int ki = (int)k;
-  if (ki < -125) return (s * bits_f((uint32_t)(ki + 227) << 23)) * 0x1p-100f;
-  if (ki > 127) return (s * bits_f((uint32_t)(ki + 126) << 23)) * 2.0f;
+  if (EN_UNLIKELY(ki < -125)) return (s * bits_f((uint32_t)(ki + 227) << 23)) * 0x1p-100f;
+  if (EN_UNLIKELY(ki > 127)) return (s * bits_f((uint32_t)(ki + 126) << 23)) * 2.0f;
   return s * bits_f((uint32_t)(ki + 127) << 23);
 }
 
 // ln x = e ln2 + ln(1+f), 1+f in [sqrt(1/2), sqrt(2)); with s = f/(2+f),
 // ln(1+f) = 2 atanh s = f - s f + 2 s (s^2/3 + s^4/5 + s^6/7 + s^8/9).
 EN_HD float log(float x) {
-  if (x != x) return x;
-  if (x < 0.0f) return qnan();
-  if (x == 0.0f) return -inf();
-  if (x == inf()) return x;
+  if (EN_UNLIKELY(x != x)) return x;
+  if (EN_UNLIKELY(x < 0.0f)) return qnan();
+  if (EN_UNLIKELY(x == 0.0f)) return -inf();
+  if (EN_UNLIKELY(x == inf())) return x;
   int bias = 0;
-  if (x < 0x1p-126f) {
+  if (EN_UNLIKELY(x < 0x1p-126f)) {
     x = x * 0x1p25f;
     bias = -25;
   }
@@ -227,7 +236,7 @@ struct PhiloxStream {
   }
 
   EN_D uint32_t next() {
-    if (left == 0) refill();
+    if (EN_UNLIKELY(left == 0)) refill();
     const uint32_t w = w0;
     w0 = w1;
     w1 = w2;
@@ -343,17 +352,17 @@ EN_COLD int32_t poisson_ptrs(float lam, PhiloxStream& st, SamplerCtx& cx) {
 
 EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
   if (!(lam > 0.0f)) return 0;
-  if (lam < 10.0f) {
+  if (EN_LIKELY(lam < 10.0f)) {
     const float u = st.uniform();
     float p = fm::exp(-lam);
     float F = p;
     int32_t k = 0;
     while (u > F) {
-      if (k == 63) break;
+      if (EN_UNLIKELY(k == 63)) break;
       k = k + 1;
       p = (p * lam) * cx.rinv[k];
       const float Fn = F + p;
-      if (Fn == F) break;
+      if (EN_UNLIKELY(Fn == F)) break;
       F = Fn;
     }
     return k;
@@ -426,17 +435,17 @@ EN_D int32_t binomial_half(int32_t n, float p, float q, float r, float lq, Philo
                            SamplerCtx& cx) {
   const float nf = (float)n;
   const float np = nf * p;
-  if (np < 10.0f) {
+  if (EN_LIKELY(np < 10.0f)) {
     float pk = fm::exp(nf * lq);
     float F = pk;
     const float u = st.uniform();
     int32_t k = 0;
     while (u > F) {
-      if (k == n || k == 63) break;
+      if (k == n || EN_UNLIKELY(k == 63)) break;
       pk = ((pk * (float)(n - k)) * r) * cx.rinv[k + 1];
       k = k + 1;
       const float Fn = F + pk;
-      if (Fn == F) break;
+      if (EN_UNLIKELY(Fn == F)) break;
       F = Fn;
     }
     return k;
@@ -531,7 +540,7 @@ EN_D BinomialArgs departure_branch(int32_t x, int32_t m, float mu, float h, cons
   b.branch = 0;
   b.T = 0.0f;
   b.p = 0.0f;
-  if (x <= m) {
+  if (EN_LIKELY(x <= m)) {
     b.n = x;
     b.c = p0c;
     return b;

@@ -100,10 +100,10 @@ __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunPar
                                                 SamplerCtx& cx, int32_t& D, int32_t& X, float& smu) {
   PhiloxStream svc;
   svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
+  const int32_t m = servers_at<EXT>(t, p, i, tau);
   // Block 0 of the stream now, while the warp's lanes still run together
   // (the first draw would compute the same block inside a divergent branch).
   svc.refill();
-  const int32_t m = servers_at<EXT>(t, p, i, tau);
   const int32_t e0 = __ldg(t.row_ptr + i);
   const int32_t deg = __ldg(t.row_ptr + i + 1) - e0;
   int32_t rem = 0;
