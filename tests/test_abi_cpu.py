@@ -86,4 +86,7 @@ def test_null_handle_is_an_argument_error(L):
     assert L.euler_net_sojourn(None, 0, 0.01, 1.0, 10, 1, 0, 0, 1, 1, None, None, None) == -1
     assert L.euler_net_grad(None, 0, 0.01, 1.0, 10, 1, 0, None, None, None, None, None, None) == -1
     assert L.euler_net_simulate_average(None, 0.01, 1.0, 10, 1, 0, None, None, None, None) == -1
+    B = Bd.lib()  # the binding's declared argument types
+    assert B.euler_net_simulate_resume(None, 0, 0.01, 1.0, 10, 1, 0, 0, None, None, None, None) == -1
+    assert B.euler_net_grad_coupled(None, 0, 0.01, 1.0, 10, 1, 0, 2, 0.05, None, 0, None, None, None) == -1
     assert isinstance(Bd.lib().euler_net_last_error(), bytes)
