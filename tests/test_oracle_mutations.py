@@ -10,6 +10,7 @@ import shutil
 import subprocess
 import sys
 import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -103,10 +104,12 @@ CASES = ([(n, "euler_oracle.c", o, w, "test_oracle_pins.py") for n, o, w in MUTA
          [(n, "exact_des.c", o, w, "test_oracle_des.py") for n, o, w in DES_MUTANTS])
 
 
-@pytest.mark.parametrize("name,target,old,new,suite", CASES, ids=[c[0] for c in CASES])
-def test_pins_reject_mutant(name, target, old, new, suite):
+def _run_mutant(name, target, old, new, suite):
+    """Build the oracle with one planted slip and run `suite` against it:
+    (returncode, output tail), or (None, message) if the anchor is not unique."""
     src = open(os.path.join(ROOT, "oracle", target)).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    if src.count(old) != 1:
+        return None, f"mutation anchor for {name} not unique"
     tmp = tempfile.mkdtemp(prefix=f"mut_{name}_")
     try:
         for f in ("euler_oracle.c", "exact_des.c", "euler_oracle.h", "exact_des.h"):
@@ -117,10 +120,26 @@ def test_pins_reject_mutant(name, target, old, new, suite):
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
                                "-fPIC", "-shared", "-o", so, os.path.join(tmp, "euler_oracle.c"),
                                os.path.join(tmp, "exact_des.c"), "-lm"])
-        env = dict(os.environ, EULER_ORACLE_SO=so)
+        env = dict(os.environ, EULER_ORACLE_SO=so, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", suite)],
-                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-        assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+        return r.returncode, r.stdout[-2000:]
     finally:
         shutil.rmtree(tmp, ignore_errors=True)
+
+
+@pytest.fixture(scope="module")
+def mutant_runs():
+    """All mutants at once, one process each, as many at a time as there are cores."""
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {c[0]: ex.submit(_run_mutant, *c) for c in CASES}
+        return {k: f.result() for k, f in futs.items()}
+
+
+@pytest.mark.parametrize("name,target,old,new,suite", CASES, ids=[c[0] for c in CASES])
+def test_pins_reject_mutant(mutant_runs, name, target, old, new, suite):
+    rc, out = mutant_runs[name]
+    assert rc is not None, out
+    assert rc != 0, f"pins did not catch mutant {name}:\n{out}"
