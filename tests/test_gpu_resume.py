@@ -96,6 +96,25 @@ def test_resume_split_at_benchmark_size(Bd, scheme):
 
 
 @pytest.mark.parametrize("scheme", [0, 1])
+def test_coupled_gradient_dag100_matches_oracle(Bd, orc, scheme):
+    """The 100-station DAG with sinusoid arrivals (64 replications, 200
+    steps): two mu_i and two arrival windows, replayed from checkpoints in
+    the HBM form's default launch shape."""
+    g = W.sinusoid_dag()
+    net, dt, T, R, windows, delta = g.net, g.dt, 2.0, 64, 5, 0.05
+    params = [0, 57, net.n + 1, net.n + 4]
+    h = Bd.EulerNet(net)
+    try:
+        got = h.grad_coupled(scheme, dt, T, R, 7, windows, delta, params=params)
+    finally:
+        h.close()
+    want = orc.grad_coupled(net, scheme, dt, T, R, 7, windows, delta, params=params)
+    assert np.array_equal(got["grad"].cpu().numpy(), want["grad"])
+    assert np.allclose(got["var"].cpu().numpy(), want["var"], rtol=1e-9, atol=0.0)
+    assert np.all(want["var"] >= 0) and np.any(want["grad"] != 0)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("case", [0, 1])
 def test_coupled_gradient_matches_oracle(Bd, orc, scheme, case):
     """Every mu_i and every arrival window, replayed from the device's own
