@@ -389,6 +389,7 @@ int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p,
   hs.state_in = x.state_in;
   hs.state_out = x.state_out;
   hs.state_ld = p.R;
+  set_round_keys(hs, p.key0, p.key1);
   // backward: K + 1 fused slots; forward: K + L - 1 skewed slots (from
   // slot tau0 + 1 in a resumed run)
   const int64_t slots = hbm_slots(h, p.scheme, p.K) - p.tau0;

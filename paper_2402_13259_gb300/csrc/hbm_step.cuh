@@ -15,6 +15,7 @@ namespace {
 // ---- HBM-state form -------------------------------------------------------------
 
 constexpr int kHbmTile = 32;  // replications per CTA column of the HBM form
+
 #ifndef EN_HBM_MIN_BLOCKS
 #define EN_HBM_MIN_BLOCKS 5  // resident 256-thread CTAs per SM the register budget targets
 #endif
@@ -121,7 +122,7 @@ __device__ __forceinline__ void soj_step(const NetTables& t, const RunParams& p,
   if (d > 0) {
     const float ps = soj_stay(x, d, m);
     PhiloxStream cs;
-    cs.init(p.key0, p.key1, 3u, (uint32_t)c, (uint32_t)tau, rep);
+    cs.init(p.key0, p.key1, 3u, (uint32_t)c, (uint32_t)tau, rep, hs.rk);
     const float u = cs.uniform();
     const uint32_t w = cs.next();
     if (!(u < ps)) {
@@ -143,7 +144,8 @@ __device__ __forceinline__ void soj_step(const NetTables& t, const RunParams& p,
 }
 
 template <int PHASE, bool EXT = true, bool GRAD = false, bool SOJ = false>
-__global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTables t, RunParams p, HbmState hs,
+__global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTables t, RunParams p,
+                                                           const __grid_constant__ HbmState hs,
                                                            int32_t s0, int32_t m, int32_t koff) {
   constexpr int phase = PHASE;
   __shared__ float rinv_s[8 * 64];
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
     if constexpr (phase == 0) {  // backward departures / routing / arrivals
       int32_t v[3] = {0, 0, 0};
       if (act) {
-        const UnitOut o = unit_update<false, false, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
+        const UnitOut o = unit_update<false, false, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx, hs.rk);
         v[0] = o.D; v[1] = o.X; v[2] = o.A;
         part[1] += o.D; part[2] += o.X; part[3] += o.A;
       }
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
         }
         if (slot <= p.K) {
           int32_t* rcur = hs.Redge + (int64_t)(slot & 1) * t.E * hs.ld;
-          const UnitOut o = unit_update<false, GRAD, EXT>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx);
+          const UnitOut o = unit_update<false, GRAD, EXT>(t, p, i, (uint32_t)slot, rep, lam_t, hs.N, rcur, hs.ld, rloc, cx, hs.rk);
           if (GRAD) hbm_add_scores(t, p, hs, i, slot, rloc, o);
           v[2] = o.D; v[3] = o.X; v[4] = o.A;
           part[1] += o.D; part[2] += o.X; part[3] += o.A;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(256, EN_HBM_MIN_BLOCKS) hbm_phase_kernel(NetTa
     } else {  // forward: one level (2) or a skewed slot (3)
       int32_t v[5] = {0, 0, 0, 0, 0};
       if (act) {
-        const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx);
+        const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, hs.N, redge, hs.ld, rloc, cx, hs.rk);
         if (GRAD) hbm_add_scores(t, p, hs, i, tau, rloc, o);
         if (SOJ) {  // customers due here at step tau: a waiting / service step, or a setup
           for (int32_t c = 0; c < hs.S; ++c) {

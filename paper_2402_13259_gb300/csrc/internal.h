@@ -124,7 +124,18 @@ struct HbmState {
   const int32_t* state_in = nullptr;
   int32_t* state_out = nullptr;
   int64_t state_ld = 0, state_r0 = 0;
+  // Philox round keys of the run's seed (see PhiloxStream), read from the
+  // kernel's parameter space
+  uint32_t rk[20] = {};
 };
+
+// The Philox round keys of (key0, key1) into hs.rk.
+inline void set_round_keys(HbmState& hs, uint32_t key0, uint32_t key1) {
+  for (int r = 0; r < 10; ++r) {
+    hs.rk[r] = key0 + (uint32_t)r * 0x9E3779B9u;
+    hs.rk[10 + r] = key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
 
 // What the HBM form's per-step kernels compute besides the step.
 enum HbmMode { kHbmPlain = 0, kHbmGrad = 1, kHbmSojourn = 2 };

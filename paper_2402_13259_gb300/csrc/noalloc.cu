@@ -203,6 +203,7 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   hs.N = reinterpret_cast<int32_t*>(base + off_N);
   hs.Redge = reinterpret_cast<int32_t*>(base + off_Redge);
   hs.ld = ld;
+  set_round_keys(hs, p.key0, p.key1);
   const NetTables t = h->tables();
   e = launch_hbm_init(t, p, hs, s);  // N = N0, partial sums = 0, tau = 1
   for (int64_t k = 0; k < K && e == cudaSuccess; ++k)

@@ -185,6 +185,9 @@ EN_HD float log1p(float x) {
 // ---------------------------------------------------------------------------
 struct PhiloxStream {
   uint32_t key0, key1;
+  // round keys (key0 + r W0 for r < 10, then key1 + r W1) in constant memory
+  // (a kernel parameter), or nullptr: then computed while the block is drawn
+  const uint32_t* rk;
   uint32_t ctr0, ctr1, ctr2, ctr3;  // ctr0 holds purpose << 24; block is OR-ed in
   uint32_t w0, w1, w2, w3;          // buffered words, consumed w0 first
   uint32_t left;                    // words remaining in the buffer
@@ -193,14 +196,15 @@ struct PhiloxStream {
   // The stream of another purpose at the same (station, step, replication).
   EN_D PhiloxStream sibling(uint32_t purpose) const {
     PhiloxStream s;
-    s.init(key0, key1, purpose, ctr1, ctr2, ctr3);
+    s.init(key0, key1, purpose, ctr1, ctr2, ctr3, rk);
     return s;
   }
 
   EN_D void init(uint32_t k0, uint32_t k1, uint32_t purpose, uint32_t station, uint32_t step,
-                 uint32_t rep) {
+                 uint32_t rep, const uint32_t* round_keys = nullptr) {
     key0 = k0;
     key1 = k1;
+    rk = round_keys;
     ctr0 = purpose << 24;
     ctr1 = station;
     ctr2 = step;
@@ -218,8 +222,10 @@ struct PhiloxStream {
       const unsigned long long m1 = (unsigned long long)0xCD9E8D57u * x2;
       const uint32_t lo0 = (uint32_t)m0, hi0 = (uint32_t)(m0 >> 32);
       const uint32_t lo1 = (uint32_t)m1, hi1 = (uint32_t)(m1 >> 32);
-      const uint32_t y0 = hi1 ^ x1 ^ k0;
-      const uint32_t y2 = hi0 ^ x3 ^ k1;
+      const uint32_t r0 = rk ? rk[round] : k0;
+      const uint32_t r1 = rk ? rk[10 + round] : k1;
+      const uint32_t y0 = hi1 ^ x1 ^ r0;
+      const uint32_t y2 = hi0 ^ x3 ^ r1;
       x0 = y0;
       x1 = lo1;
       x2 = y2;

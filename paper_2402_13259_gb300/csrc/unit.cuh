@@ -97,9 +97,10 @@ template <bool GRAD, bool EXT>
 __device__ __forceinline__ void serve_and_route(const NetTables& t, const RunParams& p, int32_t i,
                                                 uint32_t tau, uint32_t rep, int32_t y,
                                                 int32_t* redge, int64_t stride, int64_t col,
-                                                SamplerCtx& cx, int32_t& D, int32_t& X, float& smu) {
+                                                SamplerCtx& cx, int32_t& D, int32_t& X, float& smu,
+                                                const uint32_t* rk = nullptr) {
   PhiloxStream svc;
-  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep);
+  svc.init(p.key0, p.key1, 1u, (uint32_t)i, tau, rep, rk);
   const int32_t m = servers_at<EXT>(t, p, i, tau);
   // Block 0 of the stream now, while the warp's lanes still run together
   // (the first draw would compute the same block inside a divergent branch).
@@ -157,7 +158,7 @@ template <bool FULL, bool GRAD = false, bool EXT = true>
 __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunParams& p, int32_t i,
                                                uint32_t tau, uint32_t rep, const float* lam_t,
                                                int32_t* nstate, int32_t* redge, int64_t stride,
-                                               int64_t col, SamplerCtx& cx) {
+                                               int64_t col, SamplerCtx& cx, const uint32_t* rk = nullptr) {
   UnitOut o;
   o.A = 0;
   o.smu = 0.0f;
@@ -165,7 +166,7 @@ __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunPara
   const int32_t ec = __ldg(t.ex_col + i);
   if (ec >= 0) {
     PhiloxStream arr;
-    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep);
+    arr.init(p.key0, p.key1, 0u, (uint32_t)i, tau, rep, rk);
     arr.refill();  // every Poisson draw takes at least one word
     const float lam = __ldg(lam_t + ec);
     o.A = poisson(lam, arr, cx);
@@ -180,7 +181,7 @@ __device__ __forceinline__ UnitOut unit_update(const NetTables& t, const RunPara
       x = kStateLimit;
     }
   }
-  serve_and_route<GRAD, EXT>(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X, o.smu);
+  serve_and_route<GRAD, EXT>(t, p, i, tau, rep, (int32_t)x, redge, stride, col, cx, o.D, o.X, o.smu, rk);
   o.x = (int32_t)x;
   if (FULL) {
     o.N = (int32_t)x - o.D;
