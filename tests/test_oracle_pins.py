@@ -965,3 +965,26 @@ def test_coupled_gradient_agrees_with_likelihood_ratio(orc, scheme):
     coupled = np.sqrt(cp["var"] * Rc)
     ratio = coupled / independent
     assert np.all(ratio < 0.5) and np.median(ratio) < 0.2, ratio
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_coupled_windows_add_up_to_the_arrival_scale(orc, scheme):
+    """On the queueing tandem, scaling the arrival means of every step by s
+    is scaling the sinusoid's amplitude a, so the coupled window derivatives
+    summed over the windows estimate a dL/da, which the likelihood-ratio
+    gradient estimates independently (to first order in delta: the windows'
+    central differences interact only at O(delta^2))."""
+    net = _queueing_net()
+    dt, T, R, Rc, W_, delta = 0.3, 3.0, 40000, 4000, 3, 0.05
+    old = orc.set_grad_center(1)
+    try:
+        lr = orc.grad(net, scheme, dt, T, R, 29)
+    finally:
+        orc.set_grad_center(old)
+    cp = orc.grad_coupled(net, scheme, dt, T, Rc, 29, W_, delta, params=[net.n + w for w in range(W_)])
+    a = net.arrivals.a
+    want = a * lr["grad"][:, net.n]
+    got = cp["grad"].sum(axis=1)
+    se = np.sqrt(a * a * lr["var"][:, net.n] + cp["var"].sum(axis=1))
+    assert np.all(np.abs(got - want) < 5.0 * se + 0.02 * np.abs(want)), (got, want, se)
+    assert np.all(got > 0)  # more arrivals: more customers and more departures
