@@ -77,6 +77,8 @@ MUTANTS = [
     # resume: the checkpoint's own step run again
     ("resume_step_offset", "for (int64_t tau = tau0 + 1; tau <= K && !err; ++tau) {",
      "for (int64_t tau = tau0 > 0 ? tau0 : 1; tau <= K && !err; ++tau) {"),
+    # Algorithm 1's Erlang time drawn from the service stream's own words
+    ("erlang_stream_shared", "stream_sibling(&es, st, 2u);", "es = *st;"),
     # coupled gradient: the last step of a perturbation window left unscaled
     ("window_range", "if (tau >= g_win_lo && tau <= g_win_hi) L = L * g_win_factor;",
      "if (tau >= g_win_lo && tau < g_win_hi) L = L * g_win_factor;"),
