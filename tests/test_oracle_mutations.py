@@ -77,6 +77,9 @@ MUTANTS = [
     # resume: the checkpoint's own step run again
     ("resume_step_offset", "for (int64_t tau = tau0 + 1; tau <= K && !err; ++tau) {",
      "for (int64_t tau = tau0 > 0 ? tau0 : 1; tau <= K && !err; ++tau) {"),
+    # centred gradient estimator: the centring left out
+    ("grad_center_ignored", "double x = (g_grad_center ? L - Lbar : L) * sc[r * C + c];",
+     "double x = L * sc[r * C + c];"),
     # Algorithm 1's Erlang time drawn from the service stream's own words
     ("erlang_stream_shared", "stream_sibling(&es, st, 2u);", "es = *st;"),
     # coupled gradient: the last step of a perturbation window left unscaled
