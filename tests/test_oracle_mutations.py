@@ -77,6 +77,11 @@ MUTANTS = [
     # resume: the checkpoint's own step run again
     ("resume_step_offset", "for (int64_t tau = tau0 + 1; tau <= K && !err; ++tau) {",
      "for (int64_t tau = tau0 > 0 ? tau0 : 1; tau <= K && !err; ++tau) {"),
+    # Eq. (1): the busy count not capped at the servers
+    ("eq1_busy_uncapped", "    int32_t b = x < m ? x : m;", "    int32_t b = x;"),
+    # staffing schedule: a step takes the servers of its end, not its start
+    ("staffing_step_end", "int64_t j = (int64_t)floor((double)(tau - 1) * dt / net->sv_dt);",
+     "int64_t j = (int64_t)floor((double)tau * dt / net->sv_dt);"),
     # centred gradient estimator: the centring left out
     ("grad_center_ignored", "double x = (g_grad_center ? L - Lbar : L) * sc[r * C + c];",
      "double x = L * sc[r * C + c];"),
