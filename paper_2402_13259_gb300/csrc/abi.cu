@@ -735,6 +735,7 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
   p.K = (int32_t)K;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
+  set_round_keys(p.rk, p.key0, p.key1);
   p.R = R;
   p.rep_begin = rep_begin;
   p.scheme = scheme;
@@ -875,6 +876,7 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
     p.K = (int32_t)K;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
+    set_round_keys(p.rk, p.key0, p.key1);
     p.R = R;
     p.rep_begin = rep_begin;
     p.scheme = scheme;
@@ -936,6 +938,7 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
   p.K = (int32_t)K;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
+  set_round_keys(p.rk, p.key0, p.key1);
   p.R = R;
   p.rep_begin = rep_begin;
   p.scheme = scheme;

@@ -126,6 +126,7 @@ int make_batch_plan(euler_batch* b, int block, int64_t cap) {
     p.K = (int32_t)K;
     p.key0 = (uint32_t)r.seed;
     p.key1 = (uint32_t)(r.seed >> 32);
+    set_round_keys(p.rk, p.key0, p.key1);
     p.R = r.replications;
     p.rep_begin = r.rep_begin;
     p.scheme = r.scheme;

@@ -79,6 +79,7 @@ int run_range(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint
   p.tau0 = (int32_t)tau0;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
+  set_round_keys(p.rk, p.key0, p.key1);
   p.R = R;
   p.rep_begin = rep_begin;
   p.scheme = scheme;

@@ -54,7 +54,17 @@ struct RunParams {
   int64_t* stats;     // output, see eulernet.h
   unsigned* err;      // latched error bits
   int32_t tau0 = 0;   // the run covers steps tau0+1 .. K (HBM form; a resumed run)
+  uint32_t rk[20] = {};  // Philox round keys of (key0, key1), see set_round_keys
 };
+
+// The Philox round keys of (key0, key1) (key0 + r W0 for r < 10, then
+// key1 + r W1), read by the kernels from their parameter space.
+inline void set_round_keys(uint32_t* rk, uint32_t key0, uint32_t key1) {
+  for (int r = 0; r < 10; ++r) {
+    rk[r] = key0 + (uint32_t)r * 0x9E3779B9u;
+    rk[10 + r] = key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
 
 // Shared-memory bytes of the persistent kernel for a tile of `tile_reps`.
 int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps);
@@ -129,13 +139,7 @@ struct HbmState {
   uint32_t rk[20] = {};
 };
 
-// The Philox round keys of (key0, key1) into hs.rk.
-inline void set_round_keys(HbmState& hs, uint32_t key0, uint32_t key1) {
-  for (int r = 0; r < 10; ++r) {
-    hs.rk[r] = key0 + (uint32_t)r * 0x9E3779B9u;
-    hs.rk[10 + r] = key1 + (uint32_t)r * 0xBB67AE85u;
-  }
-}
+inline void set_round_keys(HbmState& hs, uint32_t key0, uint32_t key1) { set_round_keys(hs.rk, key0, key1); }
 
 // What the HBM form's per-step kernels compute besides the step.
 enum HbmMode { kHbmPlain = 0, kHbmGrad = 1, kHbmSojourn = 2 };

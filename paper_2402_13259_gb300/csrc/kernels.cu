@@ -33,7 +33,7 @@ namespace {
 
 // Single network: CTAs loop over the tiles.
 template <int SCHEME, bool GRAD = false, bool EXT = true>
-__global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunParams p) {
+__global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, const __grid_constant__ RunParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int claim[2];
   const int32_t n = t.n;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, RunPara
   __syncthreads();
   NoHook hook;
   for (int64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x)
-    tile_body<SCHEME, GRAD, EXT>(t, p, tile, sm, cx, hook);
+    tile_body<SCHEME, GRAD, EXT>(t, p, tile, sm, cx, hook, p.rk);
   flush_station_sums(t, p, sm.sacc);
   latch(p.err, cx.err);
 }

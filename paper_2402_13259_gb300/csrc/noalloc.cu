@@ -184,6 +184,7 @@ extern "C" EULERNET_API int euler_net_simulate_noalloc(euler_net* h, int32_t sch
   p.K = (int32_t)K;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
+  set_round_keys(p.rk, p.key0, p.key1);
   p.R = R;
   p.rep_begin = rep_begin;
   p.scheme = scheme;

@@ -73,9 +73,11 @@ __device__ __forceinline__ void add_scores(const NetTables& t, const RunParams& 
 // One tile: the whole time loop for replications tile*Rt ... of network t.
 // Adds per-station sums (and N_K) into sm.sacc and writes the tile's
 // per-replication sums to p.stats.  Ends with a block barrier.
+// rk: the Philox round keys in the kernel's parameter space, or nullptr.
 template <int SCHEME, bool GRAD = false, bool EXT = true, class Hook = NoHook>
 __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p, int64_t tile,
-                                          const TileSmem& sm, SamplerCtx& cx, Hook& hook) {
+                                          const TileSmem& sm, SamplerCtx& cx, Hook& hook,
+                                          const uint32_t* rk = nullptr) {
   const int32_t n = t.n;
   const int Rt = p.tile_reps;
   long long* sacc = sm.sacc;
@@ -135,7 +137,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
           const bool act = rvalid && su < n;
           int32_t v[3] = {0, 0, 0};
           if (act) {
-            const UnitOut o = unit_update<false, GRAD, EXT>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+            const UnitOut o = unit_update<false, GRAD, EXT>(t, p, su, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx, rk);
             if (GRAD) add_scores(t, p, sm, su, tau, r, Rt, o);
             hook.unit(su, r, tau, o);
             v[0] = o.D;
@@ -175,7 +177,7 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
             const int32_t i = su < m ? __ldg(t.lvl_station + s0 + su) : 0;
             int32_t v[5] = {0, 0, 0, 0, 0};
             if (act) {
-              const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx);
+              const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, Rs, Rt, r, cx, rk);
               if (GRAD) add_scores(t, p, sm, i, tau, r, Rt, o);
               hook.unit(i, r, tau, o);
               const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
