@@ -13,8 +13,10 @@ workload (2 x 10^10 station-step updates), through the library's C ABI.
         staffing schedules, Eq. (1)/(2) departures, gradients, scale sweep)
 
 Under torchrun each rank runs its own replication range (replication
-indices rank*R ... rank*R+R-1: weak scaling, no data-path collective); rank 0
-prints one JSON line.
+indices rank*R ... rank*R+R-1: weak scaling, no data-path collective); at the
+end of each step the ranks combine their statistics (an all-reduce of the
+station rows and N_K, an all-gather of the replication rows) inside the timed
+region; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -33,15 +35,43 @@ sys.path.insert(0, ROOT)
 
 METRIC = "station-step updates/s per GB300 (fwd/bwd Euler), % of binding roofline"
 UNIT = "station-step updates/s"
-SMS = 152
 LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
-# DRAM bytes of one simulate call (mean of the two schemes) from ncu counters
-# (profiles/), valid only for the kernel sources with this hash and the launch
-# forms listed; reported as null otherwise.
-# profiles/hbm_phase_kernel_dag100.md: 11.947 MB (fused backward) and 11.949 MB
-# (skewed forward) DRAM bytes per step launch at steady state, x 10,001 and
-# 10,009 step launches per call.
+# DRAM bytes of one simulate call (mean of the two schemes) from one ncu
+# capture of the step kernels: 11.947 MB (fused backward) and 11.949 MB
+# (skewed forward) per step launch at steady state, x 10,001 and 10,009 step
+# launches per call.  Valid only for the kernel sources with this hash and
+# the launch forms listed; reported as null otherwise.
 TRAFFIC = {"hash": "9f5edef5485b7a91", "forms": [2, 2], "bytes_per_call": 0.5 * (11.947e6 * 10001 + 11.949e6 * 10009)}
+
+
+def sm_count(device: int = 0) -> int:
+    """Streaming multiprocessors of the device, read at run time."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def host_cpu() -> dict:
+    """CPU model and logical core count of the host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Model Name") and v.strip():
+                model = v.strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    model = v.strip()
+                    break
+        except OSError:
+            pass
+    return {"model": model or "unknown", "host_cores": os.cpu_count()}
 
 
 def kernel_hash() -> str:
@@ -184,9 +214,12 @@ def cpu_baseline(run, K_full, reps=12):
            "events_per_s": d["events"] / des_t, "cores": 1, "kind": "exact DES",
            "sample": f"{des_reps} replications over T={run.T:g} (the Euler grid's {K_full} observation "
                      f"times), single-threaded C", "seconds": des_t}
+    cpu = host_cpu()
+    des["cpu"] = cpu
     return {"value": total_units / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} replications x {K_full} steps x {run.net.n} stations, both schemes "
-                      f"(single-threaded C oracle)", "seconds": total_t, "des": des}, per_scheme
+                      f"(single-threaded C oracle)", "seconds": total_t,
+            "cpu": dict(cpu, used=f"1 of {cpu['host_cores']} cores"), "des": des}, per_scheme
 
 
 def op_counts(run, K_full, reps=1):
@@ -223,6 +256,7 @@ def run_reference(args):
             O.simulate(run.net, scheme, run.dt, run.T, reps, run.seed, rep_begin=reps * k)
     el = time.perf_counter() - t0
     value = units_per_step * args.steps / el
+    cpu = host_cpu()
     cfg = config_dict(run, K, 1)
     cfg["replications_per_step"] = reps
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -231,7 +265,8 @@ def run_reference(args):
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{reps} replications x {K} steps x {run.net.n} stations "
-                                       "per scheme per step, single-threaded C oracle"},
+                                       "per scheme per step, single-threaded C oracle",
+                             "cpu": dict(cpu, used=f"1 of {cpu['host_cores']} cores")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -486,6 +521,9 @@ def main():
     stats = [torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda") for _ in range(2)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
 
+    counts = [sharding.replica_range(r, world, run.R, "weak")[1] for r in range(world)]
+    combined = [None, None]
+
     def one_step(events=None):
         flush.fill_(1)
         for scheme in (0, 1):
@@ -494,6 +532,10 @@ def main():
             h.simulate(scheme, run.dt, run.T, R, run.seed, rep_begin, stats=stats[scheme], check=False)
             if events is not None:
                 events[scheme][1].record(stream)
+        if world > 1:
+            # the run's one exchange: statistics over all ranks' replications
+            for scheme in (0, 1):
+                combined[scheme] = sharding.combine_stats_dist(stats[scheme], n, counts)
 
     for _ in range(args.warmup):
         one_step()
@@ -518,6 +560,14 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     h.status()
+    if world > 1:
+        # every rank holds the whole job's statistics: its own rows in place,
+        # and the station totals equal the replication totals
+        for scheme in (0, 1):
+            cb = combined[scheme]
+            sp = Bd.split_stats(cb, n, world * R)
+            assert torch.equal(sp["rep"][rank * R:(rank + 1) * R].reshape(-1), stats[scheme][5 * n:5 * n + 4 * R])
+            assert int(sp["station"][:, 0].sum()) == int(sp["rep"][:, 0].sum())
     elapsed_ms = t_start.elapsed_time(t_end)
     kern_ms = [sum(ev[k][s][0].elapsed_time(ev[k][s][1]) for k in range(args.steps)) / args.steps
                for s in (0, 1)]
@@ -571,8 +621,9 @@ def main():
         ops = [per_scheme["backward"]["ops_per_unit"] * units_launch,
                per_scheme["forward"]["ops_per_unit"] * units_launch]
         achieved = sum(ops) / (sum(kern_ms) / 1e3)
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        peak = SMS * LANES_PER_SM * sm_max * 1e6
+        sm_max = clk.get("sm_max_mhz") or getattr(torch.cuda.get_device_properties(local), "clock_rate", 0) / 1e3
+        sms = sm_count(local)
+        peak = sms * LANES_PER_SM * sm_max * 1e6
         valid = TRAFFIC["hash"] == kernel_hash() and TRAFFIC.get("forms") == [plans["backward"]["form"],
                                                                              plans["forward"]["form"]]
         hbm = plans["backward"]["form"] == 2
@@ -583,7 +634,8 @@ def main():
                           else "persistent_kernel",
                 "launch": "one euler_net_simulate call per scheme (kernel time + graph launch gaps)",
                 "ops_per_unit": {k: v["ops_per_unit"] for k, v in per_scheme.items()},
-                "peak_note": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz (issue rate)"}
+                "peak_note": f"{sms} SMs (device attribute) x {LANES_PER_SM} lanes x {sm_max:.0f} MHz "
+                             "(nvidia-smi max SM clock; issue rate)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
