@@ -237,6 +237,75 @@ def op_counts(run, K_full, reps=1):
     return per_scheme
 
 
+def _cpu_task(task):
+    """One bounded CPU job of the CPU-baseline sweep (a worker process):
+    (config, kind, scheme, rep_begin, reps) -> work and single-core seconds."""
+    name, kind, scheme, rep_begin, reps = task
+    from oracle import oracle as O
+    run = _cpu_config(name)
+    K = O.num_steps(run.dt, run.T)
+    t0 = time.process_time()
+    if kind == "des":
+        d = O.des_simulate(run.net, run.dt, run.T, reps, run.seed, rep_begin=rep_begin)
+        events = d["events"]
+    else:
+        O.simulate(run.net, scheme, run.dt, run.T, reps, run.seed, rep_begin=rep_begin)
+        events = 0
+    return name, kind, scheme, run.net.n * K * reps, events, time.process_time() - t0
+
+
+def _cpu_config(name):
+    from paper_2402_13259_gb300 import workloads as W
+    return {"C0": W.tandem3, "C1": W.layered_dag, "C2s10": lambda: W.scale_dag(10),
+            "C2s100": lambda: W.scale_dag(100), "C2s1000": lambda: W.scale_dag(1000),
+            "C2s10000": lambda: W.scale_dag(10000)}[name]()
+
+
+def run_cpu_baselines(args):
+    """The CPU baselines of the measurement plan, on this host's cores: the
+    single-threaded oracle on all of the 3-station tandem (both schemes) and
+    on sampled replications of the 100-station and 2,000-station DAGs, and
+    the exact DES on all of the tandem and on 100 replications of the
+    100-station DAG and of the scale sweep at s = 10 and s = 100.  Every job
+    is single-threaded; independent jobs run side by side in worker processes
+    (one per core), and each reports its own process CPU time, so the rates
+    are per core."""
+    import multiprocessing as mp
+    tasks = [("C0", "oracle", sc, 0, 1000) for sc in (0, 1)] + [("C0", "des", 0, 0, 1000)]
+    tasks += [("C1", "oracle", sc, 100 * k, 2) for sc in (0, 1) for k in range(4)]
+    for name in ("C2s10", "C2s100", "C2s1000", "C2s10000"):
+        tasks += [(name, "oracle", sc, 54321, 1) for sc in (0, 1)]
+    tasks += [("C1", "des", 0, 2 * k, 2) for k in range(50)]
+    tasks += [("C2s10", "des", 0, 2 * k, 2) for k in range(50)]
+    tasks += [("C2s100", "des", 0, k, 1) for k in range(100)]
+    cpu = host_cpu()
+    procs = max(1, min(os.cpu_count() or 1, args.cpu_procs or 16))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_cpu_task, tasks, chunksize=1)
+    agg = {}
+    for name, kind, scheme, units, events, sec in res:
+        key = (name, kind, scheme if kind == "oracle" else None)
+        a = agg.setdefault(key, [0, 0, 0.0, 0])
+        a[0] += units
+        a[1] += events
+        a[2] += sec
+        a[3] += 1
+    from oracle import oracle as O
+    for (name, kind, scheme), (units, events, sec, jobs) in sorted(agg.items(), key=str):
+        run = _cpu_config(name)
+        K = O.num_steps(run.dt, run.T)
+        line = {"metric": f"CPU baseline {kind}: station-step updates/s per core", "impl": "cpu", "config": name,
+                "kind": kind, "scheme": {0: "backward", 1: "forward", None: None}[scheme],
+                "value": units / sec, "unit": UNIT + (" (grid-equivalent)" if kind == "des" else ""),
+                "replications": units // (run.net.n * K), "cpu_seconds": sec,
+                "cpu": dict(cpu, used=f"1 core per job, {procs} jobs side by side")}
+        if kind == "des":
+            line["events_per_s"] = events / sec
+            line["events"] = events
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, a bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -282,6 +351,10 @@ def run_batch_comparison(args):
     from paper_2402_13259_gb300 import workloads as W
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     runs = W.batch_networks(512, T_scale=args.batch_T_scale, R_scale=args.batch_R_scale)
+    if args.batch_subset == "small":
+        # the networks a single launch cannot fill the GPU with (n R < 2^18
+        # units per step): what batching is for
+        runs = [r for r in runs if r.net.n * r.R < (1 << 18)]
     handles = [Bd.EulerNet(r.net) for r in runs]
     spec = [(k % 2, r.dt, r.T, r.R, r.seed, 0) for k, r in enumerate(runs)]
     units = sum(r.net.n * Bd.num_steps(r.dt, r.T) * r.R for r in runs)
@@ -319,14 +392,61 @@ def run_batch_comparison(args):
             "speedup": times["per_launch"] / times["batched"], "identical": identical,
             "ms_batched": times["batched"], "ms_per_launch": times["per_launch"],
             "steps": args.steps, "warmup": args.warmup, "block": block, "n_gpus": 1,
-            "config": {"workload": f"batch512: 512 layered DAGs, n log-uniform [5,5000] (median {ns[256]}), "
+            "config": {"workload": f"batch512: {len(runs)} of 512 layered DAGs ({args.batch_subset}), "
+                                   f"n log-uniform [5,5000] (median {ns[len(ns) // 2]}), "
                                    f"T ~ U[10,200] x {args.batch_T_scale}, dt in {{0.005,0.01,0.02}}, "
                                    f"R ~ U{{100..10000}} x {args.batch_R_scale}, schemes alternate",
-                       "units_per_step": units}}
+                       "units_per_step": units, "networks": len(runs),
+                       "hbm_form_networks": sum(1 for r in runs if r.net.n * r.R >= (1 << 18))}}
     b.close()
     for h in handles:
         h.close()
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_single(args):
+    """--workload scale / grad: one configuration through its entry point,
+    timed with CUDA events on the launching stream after one warm-up call
+    with 32 replications: the scale sweep's 2,000-station DAG at --scale s
+    (euler_net_simulate, both schemes), or the likelihood-ratio gradient of
+    the sinusoid-arrival 100-station DAG (euler_net_grad, both schemes).
+    --replications and --horizon override the configuration's R and T."""
+    import torch
+    from paper_2402_13259_gb300 import binding as Bd
+    from paper_2402_13259_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    run = W.scale_dag(args.scale) if args.workload == "scale" else W.sinusoid_dag()
+    if args.replications:
+        run.R = args.replications
+    if args.horizon:
+        run.T = args.horizon
+    n, R = run.net.n, run.R
+    K = Bd.num_steps(run.dt, run.T)
+    h = Bd.EulerNet(run.net)
+    stats = torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda")
+    for scheme, name in ((0, "backward"), (1, "forward")):
+        if args.workload == "scale":
+            call = lambda RR, st=None: h.simulate(scheme, run.dt, run.T, RR, run.seed, stats=st, check=False)  # noqa: E731
+        else:
+            call = lambda RR, st=None: h.grad(scheme, run.dt, run.T, RR, run.seed, check=False)  # noqa: E731
+        call(32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            call(R, stats)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h.status()
+        ms = e0.elapsed_time(e1) / args.steps
+        what = f"s={args.scale:g} 20x100 layered DAG" if args.workload == "scale" else "dag100 sinusoid, gradient"
+        print(json.dumps({"metric": f"{args.workload}: station-step updates/s", "impl": "ours", "scheme": name,
+                          "value": n * K * R / (ms / 1e3), "unit": UNIT, "ms_per_call": ms, "steps": args.steps,
+                          "config": {"workload": f"{what}, n={n}, dt={run.dt:.4g}, T={run.T:g} (K={K}), R={R}",
+                                     "plan": h.plan(scheme, R)}}), flush=True)
+    h.close()
     return 0
 
 
@@ -485,9 +605,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="dag100", choices=["dag100", "batch512", "rows"])
-    ap.add_argument("--batch-T-scale", type=float, default=0.1)
-    ap.add_argument("--batch-R-scale", type=float, default=0.02)
+    ap.add_argument("--workload", default="dag100", choices=["dag100", "batch512", "rows", "cpu", "scale", "grad"])
+    ap.add_argument("--scale", type=float, default=10000.0, help="--workload scale: the staffing scale s")
+    ap.add_argument("--cpu-procs", type=int, default=16, help="--workload cpu: worker processes")
+    ap.add_argument("--batch-T-scale", type=float, default=0.05,
+                    help="horizon scale of the batched workload (its full 2.2e13 units take ~30 min)")
+    ap.add_argument("--batch-R-scale", type=float, default=1.0)
+    ap.add_argument("--batch-subset", default="all", choices=["all", "small"],
+                    help="small: only the networks with n R < 2^18 units per step")
     ap.add_argument("--replications", type=int, default=0,
                     help="replications of the 100-station workload (default 10000)")
     ap.add_argument("--horizon", type=float, default=0.0, help="horizon T (default 100)")
@@ -498,6 +623,10 @@ def main():
         return run_batch_comparison(args)
     if args.workload == "rows":
         return run_rows(args)
+    if args.workload == "cpu":
+        return run_cpu_baselines(args)
+    if args.workload in ("scale", "grad"):
+        return run_single(args)
 
     import torch
     import torch.distributed as dist

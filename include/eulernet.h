@@ -145,9 +145,14 @@ EULERNET_API int euler_net_simulate_host(euler_net* net, int32_t scheme, double 
  * plus 4K per external station) return EULER_ERR_TOO_LARGE.  All calls
  * share the scratch and it keeps the previous call's contents: the call
  * resets what must start at zero, and calls that overlap on the GPU (other
- * streams, other threads) race and must not be issued.  Asynchronous on
- * cuda_stream except for staging the per-step tables; device-side errors are
- * returned by euler_net_status. */
+ * streams, other threads) race and must not be issued.  The handle's device
+ * must be the current device (EULER_ERR_ARG otherwise).  The per-step tables
+ * (arrival means, departure constants, staffing rows) stay in the scratch:
+ * a call with the same handle, unchanged since, and the same (dt, T) as the
+ * previous call on this device reuses them and is asynchronous on
+ * cuda_stream; any other call stages them from host memory and synchronises
+ * cuda_stream while it does.  Device-side errors are returned by
+ * euler_net_status. */
 EULERNET_API int euler_net_simulate_noalloc(euler_net* net, int32_t scheme, double dt, double T,
                                             int64_t replications, uint64_t seed, int64_t rep_begin,
                                             int64_t* stats, void* cuda_stream);
@@ -291,23 +296,36 @@ typedef struct euler_batch euler_batch; /* opaque */
 /* Prepare `count` runs, runs[j] on network nets[j] (host planning plus
  * uploads of the per-run tables and the work queue; the handles must stay
  * alive until euler_batch_destroy).  A handle may appear several times only
- * with the same (dt, T).  Work items are (network, tile of replications),
- * ordered by decreasing cost; per-network tile sizes fill the block.
- * Errors: EULER_ERR_ARG, EULER_ERR_TOO_LARGE (a network whose smallest tile
- * does not fit in shared memory), EULER_ERR_CUDA, EULER_ERR_OOM. */
+ * with the same (dt, T).  A network with n x replications >= 2^18 units per
+ * step (the threshold the autotuner may move) fills the GPU by itself and
+ * runs in the HBM form of euler_net_simulate (per-step kernels replayed from
+ * CUDA graphs), these networks one after another; the others share one
+ * persistent launch whose work items are (network, tile of replications),
+ * ordered by decreasing cost, with per-network tile sizes that fill the
+ * block.  Errors: EULER_ERR_ARG, EULER_ERR_TOO_LARGE (a network whose
+ * smallest tile does not fit in shared memory), EULER_ERR_CUDA,
+ * EULER_ERR_OOM. */
 EULERNET_API int euler_batch_create(euler_batch** out, euler_net* const* nets,
                                     const euler_run* runs, int32_t count);
 
-/* Time a few launch shapes (threads per block, shared-memory budget per CTA)
- * on a shortened horizon and keep the fastest.  Synchronises `cuda_stream`;
- * returns the chosen block size in *block_out (may be NULL). */
+/* Time launch shapes on shortened horizons and keep the fastest: the
+ * persistent launch's threads per block (stations per CTA), shared-memory
+ * budget per CTA and tile scale (replications per tile, x 1/2, 1, 2); the HBM
+ * form's threads per step kernel and slots per graph replay (steps per
+ * launch, 16 / 32 / 64), on up to six of its networks; then the n x
+ * replications threshold between the two kinds (2^16, 2^18, 2^20 or none).
+ * Synchronises `cuda_stream`; returns the persistent launch's block size in
+ * *block_out (may be NULL). */
 EULERNET_API int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out);
 
 /* Run every request: stats[j] is run j's caller-owned DEVICE buffer of
  * euler_stats_len(n_j, R_j) int64, laid out as for euler_net_simulate.  The
- * launch (zeroing plus one persistent kernel) is captured once in a CUDA
- * graph and replayed; a call with other stats pointers re-captures.
- * Asynchronous on cuda_stream; device-side errors via euler_batch_status. */
+ * persistent part (zeroing of every stats buffer plus one persistent kernel
+ * per scheme) is captured once in a CUDA graph and replayed; a call with
+ * other stats pointers re-captures.  The HBM-form networks follow on the
+ * same stream, each replaying its own graph of per-step kernels.  Results
+ * equal one euler_net_simulate call per request.  Asynchronous on
+ * cuda_stream; device-side errors via euler_batch_status. */
 EULERNET_API int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream);
 
 /* Synchronise and return the first device-side error of any run (clears them). */

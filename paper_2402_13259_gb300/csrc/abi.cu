@@ -10,6 +10,7 @@
 // means (Sec. 2.1.1, the integral of lambda_i over each step) for its (dt, T),
 // picks the launch form and runs it asynchronously.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -104,6 +105,35 @@ double eulernet::step_mean(const euler_net& h, int32_t i, int64_t tau, double dt
   return 0.0;
 }
 
+void eulernet::step_p0(const euler_net& h, double dt, int32_t i0, int32_t cnt, float4* p0, float* muh) {
+  for (int32_t k = 0; k < cnt; ++k) {
+    const float y = (float)(h.mu[i0 + k] * dt);
+    const BinomConst bc = binom_const(-fm::expm1(-y));
+    p0[k] = make_float4(bc.c0, bc.q, bc.r, bc.lq);
+    muh[k] = y;
+  }
+}
+
+void eulernet::step_servers(const euler_net& h, double dt, int64_t tau0, int64_t cnt, int32_t* servers) {
+  for (int64_t k = 0; k < cnt; ++k) {
+    const int64_t tau = tau0 + k;
+    int64_t j = (int64_t)floor((double)(tau - 1) * dt / h.sv_dt);
+    if (j > h.sv_len - 1) j = h.sv_len - 1;
+    std::copy(h.sv_table.begin() + j * h.n, h.sv_table.begin() + (j + 1) * h.n, servers + k * h.n);
+  }
+}
+
+void eulernet::step_lam(const euler_net& h, double dt, int64_t j0, int64_t cnt, float* lam) {
+  for (int64_t k = 0; k < cnt; ++k) {
+    const int64_t j = j0 + k;
+    const int64_t tau = j / h.n_ex + 1;
+    const int32_t i = h.ex_station[j % h.n_ex];
+    double L = step_mean(h, i, tau, dt);
+    if (tau >= h.win_lo && tau <= h.win_hi) L = L * h.win_factor;
+    lam[k] = (float)L;
+  }
+}
+
 namespace {
 
 int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
@@ -111,21 +141,10 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
   if (h->c_dt == dt && h->c_T == T) return EULER_OK;
   std::vector<float4> p0(h->n);
   std::vector<float> muh(h->n);
-  for (int32_t i = 0; i < h->n; ++i) {
-    const float y = (float)(h->mu[i] * dt);
-    const BinomConst bc = binom_const(-fm::expm1(-y));
-    p0[i] = make_float4(bc.c0, bc.q, bc.r, bc.lq);
-    muh[i] = y;
-  }
-  // servers of every step from the staffing schedule (value at the step's start)
+  step_p0(*h, dt, 0, h->n, p0.data(), muh.data());
   if (h->sv_len > 0) {
     std::vector<int32_t> mt((size_t)K * h->n);
-    for (int64_t tau = 1; tau <= K; ++tau) {
-      int64_t j = (int64_t)floor((double)(tau - 1) * dt / h->sv_dt);
-      if (j > h->sv_len - 1) j = h->sv_len - 1;
-      std::copy(h->sv_table.begin() + j * h->n, h->sv_table.begin() + (j + 1) * h->n,
-                mt.begin() + (tau - 1) * h->n);
-    }
+    step_servers(*h, dt, 1, K, mt.data());
     if (mt.size() > h->mtab_cap || !h->d_mtab) {
       cudaFree(h->d_mtab);
       h->d_mtab = nullptr;
@@ -140,15 +159,7 @@ int refresh_step_tables(euler_net* h, double dt, double T, cudaStream_t s) {
   CUDA_TRY(cudaMemcpyAsync(h->d_muh, muh.data(), sizeof(float) * muh.size(), cudaMemcpyHostToDevice, s));
   h->h2d_bytes += (int64_t)(sizeof(float) * muh.size());
   std::vector<float> lam((size_t)K * std::max(h->n_ex, 1), 0.0f);
-  for (int32_t i = 0; i < h->n; ++i) {
-    const int32_t c = h->ex_col[i];
-    if (c < 0) continue;
-    for (int64_t tau = 1; tau <= K; ++tau) {
-      double L = step_mean(*h, i, tau, dt);
-      if (tau >= h->win_lo && tau <= h->win_hi) L = L * h->win_factor;
-      lam[(size_t)(tau - 1) * h->n_ex + c] = (float)L;
-    }
-  }
+  if (h->n_ex > 0) step_lam(*h, dt, 0, K * h->n_ex, lam.data());
   if (!h->d_p0) CUDA_TRY(cudaMalloc(&h->d_p0, sizeof(float4) * (size_t)h->n));
   if (lam.size() > h->lam_cap) {
     if (h->d_lam) CUDA_TRY(cudaFree(h->d_lam));
@@ -393,8 +404,9 @@ int eulernet::run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p,
   // backward: K + 1 fused slots; forward: K + L - 1 skewed slots (from
   // slot tau0 + 1 in a resumed run)
   const int64_t slots = hbm_slots(h, p.scheme, p.K) - p.tau0;
-  const int64_t S = h->opt[EULER_OPT_GRAPH_STEPS] > 0 ? h->opt[EULER_OPT_GRAPH_STEPS]
-                                                      : std::min<int64_t>(std::max<int64_t>(slots, 1), 32);
+  const int64_t S = x.graph_steps > 0 ? std::min<int64_t>(x.graph_steps, std::max<int64_t>(slots, 1))
+                   : h->opt[EULER_OPT_GRAPH_STEPS] > 0 ? h->opt[EULER_OPT_GRAPH_STEPS]
+                                                        : std::min<int64_t>(std::max<int64_t>(slots, 1), 32);
   if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   for (int64_t r0 = 0; r0 < p.R; r0 += Rc) {
     RunParams pc = p;
@@ -624,7 +636,14 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
     if (h->arr_kind == EULER_ARR_SINUSOID) ext = h->w[i] != 0.0 && h->a != 0.0;
     if (h->arr_kind == EULER_ARR_TABLE)
       for (int32_t j = 0; j < h->table_len && !ext; ++j) ext = h->table[(int64_t)j * n + i] != 0.0;
-    if (ext) h->ex_col[i] = h->n_ex++;
+    if (ext) {
+      h->ex_col[i] = h->n_ex++;
+      h->ex_station.push_back(i);
+    }
+  }
+  {
+    static std::atomic<uint64_t> next_uid{1};
+    h->uid = next_uid.fetch_add(1);
   }
   std::vector<float4> qc_const(qc.size());
   for (size_t e = 0; e < qc.size(); ++e) {
@@ -677,7 +696,7 @@ int euler_net_set_servers_schedule(euler_net* h, const int32_t* table, int32_t l
     h->sv_len = len;
     h->sv_dt = tab_dt;
   }
-  h->c_dt = h->c_T = -1.0;  // rebuild the per-step tables on the next call
+  h->invalidate_step_tables();  // rebuild the per-step tables on the next call
   h->g_dt = h->g_T = -1.0;
   return EULER_OK;
 } catch (const std::bad_alloc&) {
@@ -710,6 +729,56 @@ int euler_net_plan(euler_net* h, int32_t scheme, int64_t R, int32_t* form, int32
   return fail(EULER_ERR_CUDA, "unexpected error");
 }
 
+}  // extern "C"
+
+namespace {
+
+// The run parameters of a plain simulation call (tables current for dt).
+RunParams simulate_params(const euler_net* h, int32_t scheme, double dt, int64_t K, int64_t R, uint64_t seed,
+                          int64_t rep_begin, int64_t* stats, int32_t tile_reps, int64_t num_tiles) {
+  RunParams p;
+  p.p0 = h->d_p0;
+  p.lam = h->d_lam;
+  p.h = (float)dt;
+  p.K = (int32_t)K;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  set_round_keys(p.rk, p.key0, p.key1);
+  p.R = R;
+  p.rep_begin = rep_begin;
+  p.scheme = scheme;
+  p.tile_reps = tile_reps;
+  p.num_tiles = num_tiles;
+  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
+  p.stats = stats;
+  p.err = h->d_err;
+  p.wait_limit = h->opt[EULER_OPT_WAIT_LIMIT] > 0 ? h->opt[EULER_OPT_WAIT_LIMIT] : (int64_t)1 << 25;
+  p.test_stall = h->opt[EULER_OPT_TEST_STALL] > 0 ? 1 : 0;
+  p.wait_sleep_ns = h->opt[EULER_OPT_WAIT_SLEEP] >= 0 ? (int32_t)std::min<int64_t>(h->opt[EULER_OPT_WAIT_SLEEP], 1000000) : 64;
+  p.muh = h->d_muh;
+  p.dep_mode = h->dep_mode();
+  p.mtab = h->mtab();
+  return p;
+}
+
+}  // namespace
+
+int eulernet::simulate_hbm(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+                           int64_t rep_begin, int64_t* stats, cudaStream_t s, int block, int graph_steps,
+                           int64_t k_limit) {
+  int rc = refresh_step_tables(h, dt, T, s);
+  if (rc) return rc;
+  int64_t K = euler_num_steps(dt, T);
+  if (k_limit > 0 && K > k_limit) K = k_limit;
+  if (R == 0) return EULER_OK;
+  const RunParams p = simulate_params(h, scheme, dt, K, R, seed, rep_begin, stats, 32, (R + 31) / 32);
+  HbmExtra x;
+  x.graph_steps = graph_steps;
+  return run_hbm_form(h, h->tables(), p, block, s, x);
+}
+
+extern "C" {
+
 int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
                        int64_t rep_begin, int64_t* stats, void* stream) try {
   if (!h) return fail(EULER_ERR_ARG, "handle is NULL");
@@ -728,28 +797,7 @@ int euler_net_simulate(euler_net* h, int32_t scheme, double dt, double T, int64_
   Plan pl;
   rc = make_plan(h, scheme, R, &pl);
   if (rc) return rc;
-  RunParams p;
-  p.p0 = h->d_p0;
-  p.lam = h->d_lam;
-  p.h = (float)dt;
-  p.K = (int32_t)K;
-  p.key0 = (uint32_t)seed;
-  p.key1 = (uint32_t)(seed >> 32);
-  set_round_keys(p.rk, p.key0, p.key1);
-  p.R = R;
-  p.rep_begin = rep_begin;
-  p.scheme = scheme;
-  p.tile_reps = pl.tile_reps;
-  p.num_tiles = pl.num_tiles;
-  p.cap = h->opt[EULER_OPT_SAMPLER_CAP] > 0 ? (int32_t)h->opt[EULER_OPT_SAMPLER_CAP] : 1000;
-  p.stats = stats;
-  p.err = h->d_err;
-  p.wait_limit = h->opt[EULER_OPT_WAIT_LIMIT] > 0 ? h->opt[EULER_OPT_WAIT_LIMIT] : (int64_t)1 << 25;
-  p.test_stall = h->opt[EULER_OPT_TEST_STALL] > 0 ? 1 : 0;
-  p.wait_sleep_ns = h->opt[EULER_OPT_WAIT_SLEEP] >= 0 ? (int32_t)std::min<int64_t>(h->opt[EULER_OPT_WAIT_SLEEP], 1000000) : 64;
-  p.muh = h->d_muh;
-  p.dep_mode = h->dep_mode();
-  p.mtab = h->mtab();
+  const RunParams p = simulate_params(h, scheme, dt, K, R, seed, rep_begin, stats, pl.tile_reps, pl.num_tiles);
   const NetTables t = h->tables();
   if (pl.form == 3) {
     cudaError_t e = launch_pipeline(t, p, pl.pipe, pl.grid, (int)pl.smem, s);

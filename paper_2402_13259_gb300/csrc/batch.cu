@@ -2,13 +2,24 @@
 // persistent launch fed by a work queue, planned and autotuned on the host and
 // replayed from a CUDA graph.
 //
+// Two kinds of networks.  A network with n_j R_j >= hbm_min_units units per
+// step fills the GPU by itself: it runs in the HBM form, the per-step kernels
+// of euler_net_simulate (one warp per station and 32 replications, a CUDA
+// graph of slots replayed to its horizon), one such network after another.
+// The others share one persistent launch fed by a work queue.
+//
 // Work item = (network j, tile of replications).  Network j gets a tile size
 // Rt_j (a power of two) so that its widest phase keeps the block busy
-// (forward: widest level x Rt_j ~ block; backward: all stations), reduced
-// until its tile's state fits the shared-memory budget; its per-station
-// accumulators go to a global scratch slot of the CTA when they do not fit.
-// Items are sorted by decreasing cost n_j K_j Rt_j so the last CTAs to finish
-// take the cheapest items.
+// (forward: widest level x Rt_j ~ block; backward: all stations), scaled by
+// 2^rt_shift, reduced until its tile's state fits the shared-memory budget;
+// its per-station accumulators go to a global scratch slot of the CTA when
+// they do not fit.  Items are sorted by decreasing cost n_j K_j Rt_j so the
+// last CTAs to finish take the cheapest items.
+//
+// The autotuner searches the persistent launch's threads per block (stations
+// per CTA), shared-memory budget and tile scale (replications per tile), the
+// HBM form's threads per block and slots per graph replay (steps per
+// launch), and the n R threshold between the two kinds.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,6 +40,12 @@ struct euler_batch {
   std::vector<euler_net*> nets;
   std::vector<euler_run> runs;
   int device = 0, sm_count = 0, smem_optin = 0;
+  // networks run in the HBM form, and its launch shape
+  std::vector<int> hbm_nets;
+  int64_t hbm_min_units = kHbmMinUnitsPerStep;
+  int hbm_block = kHbmBlock;
+  int hbm_graph_steps = 32;
+  int rt_shift = 0;  // persistent tiles scaled by 2^rt_shift
   // current plan
   int block = 256;
   int64_t smem_cap = 0;  // shared-memory budget per CTA used by the plan
@@ -82,12 +99,20 @@ int64_t state_bytes(const euler_net* h, int64_t Rt) {
   return 32 * Rt + 4 * ((int64_t)h->n + h->E) * Rt;
 }
 
-// Plan for a block size and a per-CTA shared-memory budget.
-int make_batch_plan(euler_batch* b, int block, int64_t cap) {
+bool runs_hbm(const euler_batch* b, int j) {
+  return b->hbm_min_units > 0 && (int64_t)b->nets[j]->n * b->runs[j].replications >= b->hbm_min_units;
+}
+
+// Plan for a block size, a per-CTA shared-memory budget, a tile scale and
+// the HBM-form threshold.
+int make_batch_plan(euler_batch* b, int block, int64_t cap, int rt_shift, int64_t hbm_min_units) {
   if (block % 32 || block < 32 || block > 512) return bfail(EULER_ERR_ARG, "batch block must be a multiple of 32 in [32, 512]");
   cap = std::min<int64_t>(cap, b->smem_optin);
   b->block = block;
   b->smem_cap = cap;
+  b->rt_shift = rt_shift;
+  b->hbm_min_units = hbm_min_units;
+  b->hbm_nets.clear();
   b->h_runs.assign(b->count, RunParams{});
   b->h_nets.assign(b->count, NetTables{});
   b->h_items.clear();
@@ -98,9 +123,14 @@ int make_batch_plan(euler_batch* b, int block, int64_t cap) {
     euler_net* h = b->nets[j];
     const euler_run& r = b->runs[j];
     const int64_t K = euler_num_steps(r.dt, r.T);
+    if (runs_hbm(b, j)) {
+      b->hbm_nets.push_back(j);
+      continue;
+    }
     const int64_t width = r.scheme == EULER_BACKWARD ? h->n : h->max_level;
     int64_t Rt = std::max<int64_t>(32, pow2_floor(std::max<int64_t>(block / std::max<int64_t>(width, 1), 1)));
-    Rt = std::min<int64_t>(Rt, block);
+    Rt = rt_shift >= 0 ? Rt << rt_shift : Rt >> -rt_shift;
+    Rt = std::max<int64_t>(1, std::min<int64_t>(Rt, block));
     const int64_t sacc_bytes = 48 * (int64_t)h->n;
     // largest tile that fits: accumulators in shared memory if possible,
     // else in the CTA's global slot
@@ -160,7 +190,7 @@ int make_batch_plan(euler_batch* b, int block, int64_t cap) {
   b->sacc_slot_len = slot;
   int per_sm = 0;
   BTRY(batch_occupancy(block, b->smem, &per_sm));
-  if (per_sm < 1) return bfail(EULER_ERR_TOO_LARGE, "batch kernel cannot be resident");
+  if (per_sm < 1 && b->num_items > 0) return bfail(EULER_ERR_TOO_LARGE, "batch kernel cannot be resident");
   b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * b->sm_count, std::max(b->num_items, 1)));
   // device copies
   if (!b->d_nets) BTRY(cudaMalloc(&b->d_nets, sizeof(NetTables) * std::max(b->count, 1)));
@@ -199,6 +229,20 @@ int upload_runs(euler_batch* b, int64_t* const* stats, int32_t k_limit) {
     if (k_limit > 0 && rp[j].K > k_limit) rp[j].K = k_limit;
   }
   BTRY(cudaMemcpy(b->d_runs, rp.data(), sizeof(RunParams) * b->count, cudaMemcpyHostToDevice));
+  return EULER_OK;
+}
+
+// The networks of the HBM form, one after another on stream s (at most
+// k_limit steps each when k_limit > 0; only the networks in `subset` when it
+// is not null).
+int run_hbm_nets(euler_batch* b, int64_t* const* stats, cudaStream_t s, int64_t k_limit,
+                 const std::vector<int>* subset = nullptr) {
+  for (int j : subset ? *subset : b->hbm_nets) {
+    const euler_run& r = b->runs[j];
+    const int rc = simulate_hbm(b->nets[j], r.scheme, r.dt, r.T, r.replications, r.seed, r.rep_begin, stats[j], s,
+                                b->hbm_block, b->hbm_graph_steps, k_limit);
+    if (rc) return rc;
+  }
   return EULER_OK;
 }
 
@@ -263,7 +307,7 @@ int euler_batch_create(euler_batch** out, euler_net* const* nets, const euler_ru
       return rc;
     }
   }
-  int rc = make_batch_plan(b, 256, 110 * 1024);
+  int rc = make_batch_plan(b, 256, 110 * 1024, 0, kHbmMinUnitsPerStep);
   if (rc) {
     euler_batch_destroy(b);
     return rc;
@@ -290,42 +334,102 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
     st[j] = pool + off;
     off += (size_t)euler_stats_len(b->nets[j]->n, b->runs[j].replications);
   }
-  const int blocks[3] = {128, 256, 512};
-  const int64_t caps[3] = {72 * 1024, 110 * 1024, 227 * 1024};
-  float best = -1.0f;
-  int best_block = b->block;
-  int64_t best_cap = b->smem_cap;
-  cudaEvent_t e0, e1;
-  BTRY(cudaEventCreate(&e0));
-  BTRY(cudaEventCreate(&e1));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = EULER_OK;
-  for (int bi = 0; bi < 3 && rc == EULER_OK; ++bi)
-    for (int ci = 0; ci < 3 && rc == EULER_OK; ++ci) {
-      if (make_batch_plan(b, blocks[bi], caps[ci]) != EULER_OK) continue;
-      rc = upload_runs(b, st.data(), 48);
-      if (rc) break;
-      cudaError_t e = cudaEventRecord(e0, s);
-      if (e == cudaSuccess) e = enqueue(b, st.data(), s);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        rc = bcuda(e, "batch autotune");
-        break;
+  // one timed trial: the persistent launch (k_limit steps per network) and,
+  // if hbm, the HBM-form networks (hbm_steps steps each, `subset` only if set)
+  auto trial = [&](int64_t k_limit, bool hbm, int64_t hbm_steps, const std::vector<int>* subset,
+                   float* ms) -> int {
+    int r = upload_runs(b, st.data(), (int32_t)k_limit);
+    if (r) return r;
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess && b->num_items > 0) e = enqueue(b, st.data(), s);
+    if (e != cudaSuccess) return bcuda(e, "batch autotune");
+    if (hbm) {
+      r = run_hbm_nets(b, st.data(), s, hbm_steps, subset);
+      if (r) return r;
+    }
+    e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    return e == cudaSuccess ? EULER_OK : bcuda(e, "batch autotune");
+  };
+  const int64_t hbm_min0 = b->hbm_min_units;
+  int best_block = b->block, best_shift = b->rt_shift;
+  int64_t best_cap = b->smem_cap, best_min = hbm_min0;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = bcuda(cudaErrorUnknown, "event");
+  // 1. the persistent launch: threads per block x shared-memory budget x tile scale
+  {
+    const int blocks[3] = {128, 256, 512};
+    const int64_t caps[3] = {72 * 1024, 110 * 1024, 227 * 1024};
+    float best = -1.0f;
+    for (int bi = 0; bi < 3 && rc == EULER_OK; ++bi)
+      for (int ci = 0; ci < 3 && rc == EULER_OK; ++ci)
+        for (int sh = -1; sh <= 1 && rc == EULER_OK; ++sh) {
+          if (make_batch_plan(b, blocks[bi], caps[ci], sh, hbm_min0) != EULER_OK || b->num_items == 0) continue;
+          float ms = 0.0f;
+          rc = trial(48, false, 0, nullptr, &ms);
+          if (rc == EULER_OK && (best < 0.0f || ms < best)) {
+            best = ms;
+            best_block = blocks[bi];
+            best_cap = caps[ci];
+            best_shift = sh;
+          }
+        }
+  }
+  // 2. the HBM form: threads per step kernel x slots per graph replay, on up
+  // to six of its networks spread over their sizes
+  if (rc == EULER_OK) rc = make_batch_plan(b, best_block, best_cap, best_shift, hbm_min0);
+  if (rc == EULER_OK && !b->hbm_nets.empty()) {
+    std::vector<int> by_size = b->hbm_nets;
+    std::sort(by_size.begin(), by_size.end(), [&](int x, int y) {
+      return b->nets[x]->n * b->runs[x].replications < b->nets[y]->n * b->runs[y].replications;
+    });
+    std::vector<int> sample;
+    const size_t m = std::min<size_t>(6, by_size.size());
+    for (size_t k = 0; k < m; ++k) sample.push_back(by_size[(k * (by_size.size() - 1)) / std::max<size_t>(m - 1, 1)]);
+    const int hblocks[2] = {128, 256};
+    const int gsteps[3] = {16, 32, 64};
+    float best = -1.0f;
+    int bb = b->hbm_block, bg = b->hbm_graph_steps;
+    for (int bi = 0; bi < 2 && rc == EULER_OK; ++bi)
+      for (int gi = 0; gi < 3 && rc == EULER_OK; ++gi) {
+        b->hbm_block = hblocks[bi];
+        b->hbm_graph_steps = gsteps[gi];
+        const int saved = b->num_items;
+        b->num_items = 0;  // time the HBM-form networks alone
+        float ms = 0.0f;
+        rc = trial(0, true, 128, &sample, &ms);
+        b->num_items = saved;
+        if (rc == EULER_OK && (best < 0.0f || ms < best)) {
+          best = ms;
+          bb = hblocks[bi];
+          bg = gsteps[gi];
+        }
       }
-      if (best < 0.0f || ms < best) {
+    b->hbm_block = bb;
+    b->hbm_graph_steps = bg;
+  }
+  // 3. the threshold between the two kinds: the whole batch, 48 steps per network
+  if (rc == EULER_OK) {
+    const int64_t mins[4] = {int64_t(1) << 16, int64_t(1) << 18, int64_t(1) << 20, 0};
+    float best = -1.0f;
+    for (int mi = 0; mi < 4 && rc == EULER_OK; ++mi) {
+      if (make_batch_plan(b, best_block, best_cap, best_shift, mins[mi]) != EULER_OK) continue;
+      float ms = 0.0f;
+      rc = trial(48, true, 48, nullptr, &ms);
+      if (rc == EULER_OK && (best < 0.0f || ms < best)) {
         best = ms;
-        best_block = blocks[bi];
-        best_cap = caps[ci];
+        best_min = mins[mi];
       }
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaFree(pool);
   for (euler_net* h : b->nets) cudaMemset(h->d_err, 0, sizeof(unsigned));
   if (rc) return rc;
-  rc = make_batch_plan(b, best_block, best_cap);
+  rc = make_batch_plan(b, best_block, best_cap, best_shift, best_min);
   if (rc) return rc;
   if (block_out) *block_out = b->block;
   return EULER_OK;
@@ -340,7 +444,23 @@ int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) tr
   for (int j = 0; j < b->count; ++j)
     if (!stats[j]) return bfail(EULER_ERR_ARG, "a stats pointer is NULL");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-  const bool same = b->exec && b->graph_stats.size() == (size_t)b->count &&
+  // the handles' per-step tables for the batch's (dt, T): another call on a
+  // handle since the plan may have rebuilt them elsewhere
+  bool moved = false;
+  for (int j = 0; j < b->count; ++j) {
+    euler_net* h = b->nets[j];
+    const int rc = prepare_step_tables(h, b->runs[j].dt, b->runs[j].T, s);
+    if (rc) return rc;
+    RunParams& p = b->h_runs[j];
+    if (!runs_hbm(b, j) && (p.p0 != h->d_p0 || p.lam != h->d_lam || p.muh != h->d_muh || p.mtab != h->mtab())) {
+      p.p0 = h->d_p0;
+      p.lam = h->d_lam;
+      p.muh = h->d_muh;
+      p.mtab = h->mtab();
+      moved = true;
+    }
+  }
+  const bool same = !moved && b->exec && b->graph_stats.size() == (size_t)b->count &&
                     std::equal(b->graph_stats.begin(), b->graph_stats.end(), stats);
   if (!same) {
     int rc = upload_runs(b, stats, 0);
@@ -363,8 +483,8 @@ int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) tr
     if (e != cudaSuccess) return bcuda(e, "cudaGraphInstantiate");
     b->graph_stats.assign(stats, stats + b->count);
   }
-  BTRY(cudaGraphLaunch(b->exec, s));
-  return EULER_OK;
+  BTRY(cudaGraphLaunch(b->exec, s));  // zeroes every stats buffer, runs the persistent items
+  return run_hbm_nets(b, stats, s, 0);
 } catch (const std::bad_alloc&) {
   return bfail(EULER_ERR_OOM, "host memory allocation failed");
 } catch (...) {

@@ -179,7 +179,7 @@ struct Perturb {
     h->mu[i] = v;
     const float f = (float)v;
     CTRY(cudaMemcpy(h->d_mu + i, &f, sizeof f, cudaMemcpyHostToDevice));
-    h->c_dt = -1.0;  // the p0 constants and mu h depend on mu
+    h->invalidate_step_tables();  // the p0 constants and mu h depend on mu
     return EULER_OK;
   }
   void set_window(int64_t lo, int64_t hi, double factor) {
@@ -187,7 +187,7 @@ struct Perturb {
     h->win_lo = lo;
     h->win_hi = hi;
     h->win_factor = factor;
-    h->c_dt = -1.0;
+    h->invalidate_step_tables();
   }
   ~Perturb() {
     if (mu_i >= 0) {
@@ -195,13 +195,13 @@ struct Perturb {
       h->mu[mu_i] = mu_old;
       const float f = (float)mu_old;
       cudaMemcpy(h->d_mu + mu_i, &f, sizeof f, cudaMemcpyHostToDevice);
-      h->c_dt = -1.0;
+      h->invalidate_step_tables();
     }
     if (window) {
       h->win_lo = 1;
       h->win_hi = 0;
       h->win_factor = 1.0;
-      h->c_dt = -1.0;
+      h->invalidate_step_tables();
     }
   }
 };

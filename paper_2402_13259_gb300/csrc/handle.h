@@ -13,6 +13,9 @@
 struct euler_net {
   int32_t n = 0, E = 0, L = 0, max_level = 0, n_ex = 0;
   std::vector<int32_t> row_ptr, col, servers, lvl_ptr, lvl_station, ex_col, N0;
+  std::vector<int32_t> ex_station;  // station of each column of the arrival-mean table
+  uint64_t uid = 0;                 // unique per handle in this process
+  uint64_t tables_gen = 0;          // bumped whenever the per-step tables' inputs change
   std::vector<double> prob, mu;
   int32_t arr_kind = EULER_ARR_NONE;
   std::vector<double> w, table;
@@ -85,6 +88,13 @@ struct euler_net {
   int64_t opt[13] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
   int64_t h2d_bytes = 0;  // host-to-device bytes copied by this handle so far
 
+  // The per-step tables depend on mu, the staffing schedule and the arrival
+  // window: after a change they are rebuilt on the next call.
+  void invalidate_step_tables() {
+    c_dt = c_T = -1.0;
+    ++tables_gen;
+  }
+
   int32_t dep_mode() const { return opt[EULER_OPT_DEPARTURE] > 0 ? (int32_t)opt[EULER_OPT_DEPARTURE] : 0; }
   const int32_t* mtab() const { return sv_len > 0 ? d_mtab : nullptr; }
 
@@ -130,12 +140,22 @@ struct HbmExtra {
   int32_t* out = nullptr;              // [R][S]
   const int32_t* state_in = nullptr;   // checkpoint N_{p.tau0}, [n][R], or nullptr (N0)
   int32_t* state_out = nullptr;        // N_K out, [n][R], or nullptr
+  int graph_steps = 0;                 // slots per CUDA graph replay (0: the handle's option)
 };
 
 // One call in the HBM form: state set-up, the graph of per-step kernels
 // replayed to the horizon, statistics (and scores / sojourn times) out.
 int run_hbm_form(euler_net* h, const NetTables& t, const RunParams& p, int block, cudaStream_t s,
                  const HbmExtra& x);
+
+// A plain simulation call in the HBM form (the per-step kernels; the batched
+// form's large networks): tables made current for (dt, T), `block` threads
+// per step kernel, `graph_steps` slots per graph replay (0: default), at most
+// k_limit steps when k_limit > 0 (tuning runs).  `stats` must be zeroed by
+// the caller, on stream s.
+int simulate_hbm(euler_net* h, int32_t scheme, double dt, double T, int64_t R, uint64_t seed,
+                 int64_t rep_begin, int64_t* stats, cudaStream_t s, int block, int graph_steps,
+                 int64_t k_limit);
 
 // Per-step mean of the external arrivals of station i over step tau: the
 // exact integral of lambda_i over ((tau-1) dt, tau dt] (Sec. 2.1.1), in double.
@@ -145,4 +165,16 @@ void set_last_error(const char* msg);
 // Make the handle's per-call tables (p0 constants, Lambda) current for
 // (dt, T) on stream s; returns an EULER_* code.
 int prepare_step_tables(euler_net* h, double dt, double T, cudaStream_t s);
+
+// The per-step tables of a call with step dt, written into host buffers in
+// ranges, so that every entry point computes them the same way:
+//   p0[k], muh[k] for stations i0 + k (k < cnt): the constants of the x <= m
+//     departure probability 1 - e^{-mu_i dt} (Lemma 1) and mu_i dt in float;
+//   servers[k * n + i] for steps tau0 + k (k < cnt): the staffing schedule's
+//     value at the step's start (needs a schedule);
+//   lam[k] for the flat entries j0 + k (k < cnt) of the [K][n_ex] table of
+//     external-arrival means (Sec. 2.1.1), the arrival window's factor applied.
+void step_p0(const euler_net& h, double dt, int32_t i0, int32_t cnt, float4* p0, float* muh);
+void step_servers(const euler_net& h, double dt, int64_t tau0, int64_t cnt, int32_t* servers);
+void step_lam(const euler_net& h, double dt, int64_t j0, int64_t cnt, float* lam);
 }  // namespace eulernet

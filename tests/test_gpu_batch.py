@@ -37,12 +37,26 @@ def _mixed_batch():
     big = W.layered_dag(L=15, W=100, seed=11, R=40, T=0.3, dt=0.01).net
     nets.append(big)
     runs.append((1, 0.01, 0.3, 40, 9, 0))
+    # networks with n R >= 2^18 units per step: HBM-form items (per-step
+    # kernels), one of them twice with another scheme and replication range
+    wide = W.layered_dag(R=2800, T=0.3).net
+    nets += [wide, wide]
+    runs += [(1, 0.01, 0.3, 2800, 3, 17), (0, 0.01, 0.3, 2700, 3, 5000)]
+    sc = W.scale_dag(10, R=200)
+    nets.append(sc.net)
+    runs.append((0, sc.dt, 3.0, 200, 4, 0))
     return nets, runs
 
 
 def test_batch_matches_single_runs_and_oracle(Bd, orc):
+    """Small networks share the persistent launch, large ones (n R >= 2^18)
+    run as HBM-form items; before and after autotuning (which may move the
+    threshold between the two) every run equals its own launch."""
     nets, runs = _mixed_batch()
-    handles = [Bd.EulerNet(net) for net in nets]
+    handles = []
+    for net in nets:  # a network listed twice shares one handle
+        same = [k for k in range(len(handles)) if nets[k] is net]
+        handles.append(handles[same[0]] if same else Bd.EulerNet(net))
     try:
         single = []
         for h, r in zip(handles, runs):
@@ -65,8 +79,14 @@ def test_batch_matches_single_runs_and_oracle(Bd, orc):
             net, r = nets[j], runs[j]
             want = orc.simulate(net, r[0], r[1], r[2], r[3], r[4], rep_begin=r[5])["stats"]
             assert np.array_equal(single[j], want), f"run {j} vs oracle"
+        for j in (9, 11):  # HBM-form items: sampled replications against the oracle
+            net, r = nets[j], runs[j]
+            rp = Bd.split_stats(single[j], net.n, r[3])["rep"]
+            for k in (0, r[3] - 1):
+                want = orc.simulate(net, r[0], r[1], r[2], 1, r[4], rep_begin=r[5] + k)["rep"][0]
+                assert np.array_equal(rp[k], want), f"run {j} replication {k} vs oracle"
     finally:
-        for h in handles:
+        for h in {id(h): h for h in handles}.values():
             h.close()
 
 
