@@ -377,11 +377,13 @@ def run_batch_comparison(args):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(f"timed_{name}")  # lets a profiler pick the timed launches
         e0.record(stream)
         for _ in range(args.steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         times[name] = e0.elapsed_time(e1) / args.steps
     b.status()
     identical = all(torch.equal(x, y) for x, y in zip(stats_b, stats_s))
@@ -391,7 +393,7 @@ def run_batch_comparison(args):
             "per_launch_value": units / (times["per_launch"] / 1e3),
             "speedup": times["per_launch"] / times["batched"], "identical": identical,
             "ms_batched": times["batched"], "ms_per_launch": times["per_launch"],
-            "steps": args.steps, "warmup": args.warmup, "block": block, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "block": block, "plan": b.info(), "n_gpus": 1,
             "config": {"workload": f"batch512: {len(runs)} of 512 layered DAGs ({args.batch_subset}), "
                                    f"n log-uniform [5,5000] (median {ns[len(ns) // 2]}), "
                                    f"T ~ U[10,200] x {args.batch_T_scale}, dt in {{0.005,0.01,0.02}}, "
@@ -616,6 +618,8 @@ def main():
     ap.add_argument("--replications", type=int, default=0,
                     help="replications of the 100-station workload (default 10000)")
     ap.add_argument("--horizon", type=float, default=0.0, help="horizon T (default 100)")
+    ap.add_argument("--form", type=int, default=0,
+                    help="launch form of the 100-station workload: 0 = the planner's, 1 = persistent, 2 = HBM")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -646,6 +650,8 @@ def main():
     rep_begin, R = sharding.replica_range(rank, world, R, "weak")
     units_per_step = 2 * n * K * R  # per rank
     h = Bd.EulerNet(run.net)
+    if args.form:
+        h.set_option(Bd.OPT_FORM, args.form)
     stream = torch.cuda.current_stream()
     stats = [torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda") for _ in range(2)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
@@ -718,6 +724,8 @@ def main():
         t0 = time.perf_counter()
         for k in range(args.steps):
             he = Bd.EulerNet(run.net)
+            if args.form:
+                he.set_option(Bd.OPT_FORM, args.form)
             for scheme in (0, 1):
                 he.simulate_host(scheme, run.dt, run.T, R, run.seed, rep_begin, out=out[scheme])
             h2d = he.h2d_bytes()

@@ -328,6 +328,18 @@ EULERNET_API int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t
  * cuda_stream; device-side errors via euler_batch_status. */
 EULERNET_API int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream);
 
+/* The batch's current plan (after euler_batch_create, or the autotuner's
+ * choice): *hbm_networks = requests run in the HBM form, *hbm_min_units =
+ * their n x replications threshold (0: none), *critical_path = 1 if the
+ * critical-path rule moves long work items to the HBM form, *block and
+ * *tile_shift = the persistent launch's threads per block and tile scale
+ * (replications per tile x 2^tile_shift), *hbm_block and *graph_steps = the
+ * HBM form's threads per step kernel and slots per graph replay.  Any output
+ * pointer may be NULL.  Returns EULER_ERR_ARG for a NULL batch. */
+EULERNET_API int euler_batch_info(const euler_batch* b, int32_t* hbm_networks, int64_t* hbm_min_units,
+                                  int32_t* critical_path, int32_t* block, int32_t* tile_shift,
+                                  int32_t* hbm_block, int32_t* graph_steps);
+
 /* Synchronise and return the first device-side error of any run (clears them). */
 EULERNET_API int euler_batch_status(euler_batch* b, void* cuda_stream);
 

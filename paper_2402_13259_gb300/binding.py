@@ -82,6 +82,9 @@ def lib():
         L.euler_batch_autotune.restype = C.c_int
         L.euler_batch_run.argtypes = [vp, C.POINTER(vp), vp]
         L.euler_batch_run.restype = C.c_int
+        L.euler_batch_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.euler_batch_info.restype = C.c_int
         L.euler_batch_status.argtypes = [vp, vp]
         L.euler_batch_status.restype = C.c_int
         L.euler_batch_destroy.argtypes = [vp]
@@ -351,6 +354,14 @@ class Batch:
         blk = C.c_int32()
         _check(lib().euler_batch_autotune(self._b, C.c_void_p(_stream_ptr(stream)), C.byref(blk)))
         return blk.value
+
+    def info(self) -> Dict[str, int]:
+        """The current plan (see euler_batch_info)."""
+        v = [C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()]
+        _check(lib().euler_batch_info(self._b, *[C.byref(x) for x in v]))
+        keys = ["hbm_networks", "hbm_min_units", "critical_path", "block", "tile_shift", "hbm_block",
+                "graph_steps"]
+        return dict(zip(keys, (x.value for x in v)))
 
     def alloc_stats(self):
         import torch

@@ -42,7 +42,9 @@ struct euler_batch {
   int device = 0, sm_count = 0, smem_optin = 0;
   // networks run in the HBM form, and its launch shape
   std::vector<int> hbm_nets;
+  std::vector<char> is_hbm;  // per network
   int64_t hbm_min_units = kHbmMinUnitsPerStep;
+  double cp_factor = 1.0;  // critical-path rule (see make_batch_plan); <= 0 off
   int hbm_block = kHbmBlock;
   int hbm_graph_steps = 32;
   int rt_shift = 0;  // persistent tiles scaled by 2^rt_shift
@@ -99,19 +101,94 @@ int64_t state_bytes(const euler_net* h, int64_t Rt) {
   return 32 * Rt + 4 * ((int64_t)h->n + h->E) * Rt;
 }
 
-bool runs_hbm(const euler_batch* b, int j) {
-  return b->hbm_min_units > 0 && (int64_t)b->nets[j]->n * b->runs[j].replications >= b->hbm_min_units;
+bool runs_hbm(const euler_batch* b, int j) { return b->is_hbm[j] != 0; }
+
+// Tile of network j in the persistent launch: the widest phase x Rt ~ block,
+// scaled by 2^rt_shift, reduced until it fits the budget (per-station sums in
+// shared memory if possible, else in the CTA's global slot).
+bool tile_for(const euler_batch* b, int j, int block, int64_t cap, int rt_shift, int64_t* Rt_out,
+              bool* sacc_global_out) {
+  const euler_net* h = b->nets[j];
+  const int64_t width = b->runs[j].scheme == EULER_BACKWARD ? h->n : h->max_level;
+  int64_t Rt = std::max<int64_t>(32, pow2_floor(std::max<int64_t>(block / std::max<int64_t>(width, 1), 1)));
+  Rt = rt_shift >= 0 ? Rt << rt_shift : Rt >> -rt_shift;
+  Rt = std::max<int64_t>(1, std::min<int64_t>(Rt, block));
+  const int64_t sacc_bytes = 48 * (int64_t)h->n;
+  for (; Rt >= 1; Rt /= 2) {
+    if (256 + sacc_bytes + state_bytes(h, Rt) <= cap) {
+      *Rt_out = Rt;
+      *sacc_global_out = false;
+      return true;
+    }
+    if (256 + state_bytes(h, Rt) <= cap) {
+      *Rt_out = Rt;
+      *sacc_global_out = true;
+      return true;
+    }
+  }
+  return false;
 }
 
-// Plan for a block size, a per-CTA shared-memory budget, a tile scale and
-// the HBM-form threshold.
-int make_batch_plan(euler_batch* b, int block, int64_t cap, int rt_shift, int64_t hbm_min_units) {
+// Plan for a block size, a per-CTA shared-memory budget, a tile scale, the
+// HBM-form threshold and the critical-path factor.
+//
+// Critical-path rule: a work item is one tile of replications through the
+// network's whole horizon on one CTA, so when the launch has more items than
+// CTAs, a network whose item costs (n K Rt) more than cp_factor x the mean
+// load per CTA (sum of n K R over the launch's networks / CTAs) would outlast
+// the rest of the launch; such a network runs in the HBM form instead, where
+// one step of all its replications spreads over the whole GPU, provided a
+// step has at least 2^14 units (512 warps) so that its launches do more than
+// wait on launch latency.  With fewer items than CTAs every item runs at
+// once and nothing moves.
+int make_batch_plan(euler_batch* b, int block, int64_t cap, int rt_shift, int64_t hbm_min_units,
+                    double cp_factor) {
   if (block % 32 || block < 32 || block > 512) return bfail(EULER_ERR_ARG, "batch block must be a multiple of 32 in [32, 512]");
   cap = std::min<int64_t>(cap, b->smem_optin);
   b->block = block;
   b->smem_cap = cap;
   b->rt_shift = rt_shift;
   b->hbm_min_units = hbm_min_units;
+  b->cp_factor = cp_factor;
+  b->is_hbm.assign(b->count, 0);
+  for (int j = 0; j < b->count; ++j)
+    b->is_hbm[j] = hbm_min_units > 0 && (int64_t)b->nets[j]->n * b->runs[j].replications >= hbm_min_units;
+  std::vector<int64_t> Rt_of(b->count, 1);
+  std::vector<char> sacc_g(b->count, 0);
+  for (int j = 0; j < b->count; ++j) {
+    if (b->is_hbm[j]) continue;
+    bool g = false;
+    if (!tile_for(b, j, block, cap, rt_shift, &Rt_of[j], &g))
+      return bfail(EULER_ERR_TOO_LARGE, "a network's smallest tile does not fit the shared-memory budget");
+    sacc_g[j] = g;
+  }
+  if (cp_factor > 0.0) {
+    for (int pass = 0; pass < 8; ++pass) {
+      int64_t smem = 256;
+      double work = 0.0, n_items = 0.0;
+      for (int j = 0; j < b->count; ++j) {
+        if (b->is_hbm[j]) continue;
+        const euler_net* h = b->nets[j];
+        smem = std::max<int64_t>(smem, 256 + (sacc_g[j] ? 0 : 48 * (int64_t)h->n) + state_bytes(h, Rt_of[j]));
+        work += (double)h->n * (double)euler_num_steps(b->runs[j].dt, b->runs[j].T) * (double)b->runs[j].replications;
+        n_items += (double)((b->runs[j].replications + Rt_of[j] - 1) / Rt_of[j]);
+      }
+      int per_sm = 0;
+      BTRY(batch_occupancy(block, (int)smem, &per_sm));
+      const double ctas = std::max(1.0, (double)per_sm * b->sm_count);
+      if (n_items <= ctas) break;
+      bool moved = false;
+      for (int j = 0; j < b->count; ++j) {
+        if (b->is_hbm[j] || (int64_t)b->nets[j]->n * b->runs[j].replications < (int64_t(1) << 14)) continue;
+        const double item = (double)b->nets[j]->n * (double)euler_num_steps(b->runs[j].dt, b->runs[j].T) * (double)Rt_of[j];
+        if (item > cp_factor * work / ctas) {
+          b->is_hbm[j] = 1;
+          moved = true;
+        }
+      }
+      if (!moved) break;
+    }
+  }
   b->hbm_nets.clear();
   b->h_runs.assign(b->count, RunParams{});
   b->h_nets.assign(b->count, NetTables{});
@@ -123,29 +200,13 @@ int make_batch_plan(euler_batch* b, int block, int64_t cap, int rt_shift, int64_
     euler_net* h = b->nets[j];
     const euler_run& r = b->runs[j];
     const int64_t K = euler_num_steps(r.dt, r.T);
-    if (runs_hbm(b, j)) {
+    if (b->is_hbm[j]) {
       b->hbm_nets.push_back(j);
       continue;
     }
-    const int64_t width = r.scheme == EULER_BACKWARD ? h->n : h->max_level;
-    int64_t Rt = std::max<int64_t>(32, pow2_floor(std::max<int64_t>(block / std::max<int64_t>(width, 1), 1)));
-    Rt = rt_shift >= 0 ? Rt << rt_shift : Rt >> -rt_shift;
-    Rt = std::max<int64_t>(1, std::min<int64_t>(Rt, block));
+    const int64_t Rt = Rt_of[j];
+    const bool sacc_global = sacc_g[j] != 0;
     const int64_t sacc_bytes = 48 * (int64_t)h->n;
-    // largest tile that fits: accumulators in shared memory if possible,
-    // else in the CTA's global slot
-    bool sacc_global = false, fits = false;
-    for (; Rt >= 1; Rt /= 2) {
-      if (256 + sacc_bytes + state_bytes(h, Rt) <= cap) {
-        fits = true;
-        break;
-      }
-      if (256 + state_bytes(h, Rt) <= cap) {
-        sacc_global = fits = true;
-        break;
-      }
-    }
-    if (!fits) return bfail(EULER_ERR_TOO_LARGE, "a network's smallest tile does not fit the shared-memory budget");
     smem = std::max<int64_t>(smem, 256 + (sacc_global ? 0 : sacc_bytes) + state_bytes(h, Rt));
     if (sacc_global) slot = std::max<int64_t>(slot, 6 * (int64_t)h->n);
     RunParams p;
@@ -220,27 +281,35 @@ int make_batch_plan(euler_batch* b, int block, int64_t cap, int rt_shift, int64_
   return EULER_OK;
 }
 
-// Upload the run table with these stats pointers (and optionally a shortened
-// horizon for tuning).
-int upload_runs(euler_batch* b, int64_t* const* stats, int32_t k_limit) {
+// Steps of network j in a tuning run whose horizons are all scaled by
+// k_scale (every network keeps at least one step), or its K if k_scale <= 0.
+int64_t scaled_steps(const euler_batch* b, int j, double k_scale) {
+  const int64_t K = euler_num_steps(b->runs[j].dt, b->runs[j].T);
+  if (k_scale <= 0.0) return K;
+  return std::max<int64_t>(1, std::min<int64_t>(K, (int64_t)ceil((double)K * k_scale)));
+}
+
+// Upload the run table with these stats pointers (horizons scaled by k_scale
+// for tuning, see scaled_steps).
+int upload_runs(euler_batch* b, int64_t* const* stats, double k_scale) {
   std::vector<RunParams> rp = b->h_runs;
   for (int j = 0; j < b->count; ++j) {
     rp[j].stats = stats[j];
-    if (k_limit > 0 && rp[j].K > k_limit) rp[j].K = k_limit;
+    if (!b->is_hbm[j]) rp[j].K = (int32_t)scaled_steps(b, j, k_scale);
   }
   BTRY(cudaMemcpy(b->d_runs, rp.data(), sizeof(RunParams) * b->count, cudaMemcpyHostToDevice));
   return EULER_OK;
 }
 
-// The networks of the HBM form, one after another on stream s (at most
-// k_limit steps each when k_limit > 0; only the networks in `subset` when it
-// is not null).
-int run_hbm_nets(euler_batch* b, int64_t* const* stats, cudaStream_t s, int64_t k_limit,
+// The networks of the HBM form, one after another on stream s (horizons
+// scaled by k_scale for tuning; only the networks in `subset` when it is not
+// null).
+int run_hbm_nets(euler_batch* b, int64_t* const* stats, cudaStream_t s, double k_scale,
                  const std::vector<int>* subset = nullptr) {
   for (int j : subset ? *subset : b->hbm_nets) {
     const euler_run& r = b->runs[j];
     const int rc = simulate_hbm(b->nets[j], r.scheme, r.dt, r.T, r.replications, r.seed, r.rep_begin, stats[j], s,
-                                b->hbm_block, b->hbm_graph_steps, k_limit);
+                                b->hbm_block, b->hbm_graph_steps, k_scale > 0.0 ? scaled_steps(b, j, k_scale) : 0);
     if (rc) return rc;
   }
   return EULER_OK;
@@ -307,7 +376,7 @@ int euler_batch_create(euler_batch** out, euler_net* const* nets, const euler_ru
       return rc;
     }
   }
-  int rc = make_batch_plan(b, 256, 110 * 1024, 0, kHbmMinUnitsPerStep);
+  int rc = make_batch_plan(b, 256, 110 * 1024, 0, kHbmMinUnitsPerStep, 1.0);
   if (rc) {
     euler_batch_destroy(b);
     return rc;
@@ -336,17 +405,21 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = EULER_OK;
-  // one timed trial: the persistent launch (k_limit steps per network) and,
-  // if hbm, the HBM-form networks (hbm_steps steps each, `subset` only if set)
-  auto trial = [&](int64_t k_limit, bool hbm, int64_t hbm_steps, const std::vector<int>* subset,
-                   float* ms) -> int {
-    int r = upload_runs(b, st.data(), (int32_t)k_limit);
+  // Trials run every horizon scaled by one factor (the longest to 48 steps),
+  // so that work items keep their relative lengths (the critical path).
+  int64_t kmax = 1;
+  for (int j = 0; j < b->count; ++j) kmax = std::max<int64_t>(kmax, euler_num_steps(b->runs[j].dt, b->runs[j].T));
+  const double k_scale = std::min(1.0, 48.0 / (double)kmax);
+  // one timed trial: the persistent launch and, if hbm, the HBM-form
+  // networks (`subset` only, if set), horizons scaled by ks
+  auto trial = [&](double ks, bool persistent, bool hbm, const std::vector<int>* subset, float* ms) -> int {
+    int r = upload_runs(b, st.data(), ks);
     if (r) return r;
     cudaError_t e = cudaEventRecord(e0, s);
-    if (e == cudaSuccess && b->num_items > 0) e = enqueue(b, st.data(), s);
+    if (e == cudaSuccess && persistent && b->num_items > 0) e = enqueue(b, st.data(), s);
     if (e != cudaSuccess) return bcuda(e, "batch autotune");
     if (hbm) {
-      r = run_hbm_nets(b, st.data(), s, hbm_steps, subset);
+      r = run_hbm_nets(b, st.data(), s, ks, subset);
       if (r) return r;
     }
     e = cudaEventRecord(e1, s);
@@ -355,8 +428,10 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
     return e == cudaSuccess ? EULER_OK : bcuda(e, "batch autotune");
   };
   const int64_t hbm_min0 = b->hbm_min_units;
+  const double cp0 = b->cp_factor;
   int best_block = b->block, best_shift = b->rt_shift;
   int64_t best_cap = b->smem_cap, best_min = hbm_min0;
+  double best_cp = cp0;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = bcuda(cudaErrorUnknown, "event");
   // 1. the persistent launch: threads per block x shared-memory budget x tile scale
   {
@@ -366,9 +441,9 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
     for (int bi = 0; bi < 3 && rc == EULER_OK; ++bi)
       for (int ci = 0; ci < 3 && rc == EULER_OK; ++ci)
         for (int sh = -1; sh <= 1 && rc == EULER_OK; ++sh) {
-          if (make_batch_plan(b, blocks[bi], caps[ci], sh, hbm_min0) != EULER_OK || b->num_items == 0) continue;
+          if (make_batch_plan(b, blocks[bi], caps[ci], sh, hbm_min0, cp0) != EULER_OK || b->num_items == 0) continue;
           float ms = 0.0f;
-          rc = trial(48, false, 0, nullptr, &ms);
+          rc = trial(k_scale, true, false, nullptr, &ms);
           if (rc == EULER_OK && (best < 0.0f || ms < best)) {
             best = ms;
             best_block = blocks[bi];
@@ -378,8 +453,8 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
         }
   }
   // 2. the HBM form: threads per step kernel x slots per graph replay, on up
-  // to six of its networks spread over their sizes
-  if (rc == EULER_OK) rc = make_batch_plan(b, best_block, best_cap, best_shift, hbm_min0);
+  // to six of its networks spread over their sizes, 128 steps each at most
+  if (rc == EULER_OK) rc = make_batch_plan(b, best_block, best_cap, best_shift, hbm_min0, cp0);
   if (rc == EULER_OK && !b->hbm_nets.empty()) {
     std::vector<int> by_size = b->hbm_nets;
     std::sort(by_size.begin(), by_size.end(), [&](int x, int y) {
@@ -388,6 +463,9 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
     std::vector<int> sample;
     const size_t m = std::min<size_t>(6, by_size.size());
     for (size_t k = 0; k < m; ++k) sample.push_back(by_size[(k * (by_size.size() - 1)) / std::max<size_t>(m - 1, 1)]);
+    int64_t ks_max = 1;
+    for (int j : sample) ks_max = std::max<int64_t>(ks_max, euler_num_steps(b->runs[j].dt, b->runs[j].T));
+    const double ks2 = std::min(1.0, 128.0 / (double)ks_max);
     const int hblocks[2] = {128, 256};
     const int gsteps[3] = {16, 32, 64};
     float best = -1.0f;
@@ -396,11 +474,8 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
       for (int gi = 0; gi < 3 && rc == EULER_OK; ++gi) {
         b->hbm_block = hblocks[bi];
         b->hbm_graph_steps = gsteps[gi];
-        const int saved = b->num_items;
-        b->num_items = 0;  // time the HBM-form networks alone
         float ms = 0.0f;
-        rc = trial(0, true, 128, &sample, &ms);
-        b->num_items = saved;
+        rc = trial(ks2, false, true, &sample, &ms);
         if (rc == EULER_OK && (best < 0.0f || ms < best)) {
           best = ms;
           bb = hblocks[bi];
@@ -410,26 +485,30 @@ int euler_batch_autotune(euler_batch* b, void* cuda_stream, int32_t* block_out) 
     b->hbm_block = bb;
     b->hbm_graph_steps = bg;
   }
-  // 3. the threshold between the two kinds: the whole batch, 48 steps per network
+  // 3. which networks take the HBM form: the n R threshold x the
+  // critical-path rule (on / off), the whole batch
   if (rc == EULER_OK) {
     const int64_t mins[4] = {int64_t(1) << 16, int64_t(1) << 18, int64_t(1) << 20, 0};
+    const double cps[2] = {1.0, 0.0};
     float best = -1.0f;
-    for (int mi = 0; mi < 4 && rc == EULER_OK; ++mi) {
-      if (make_batch_plan(b, best_block, best_cap, best_shift, mins[mi]) != EULER_OK) continue;
-      float ms = 0.0f;
-      rc = trial(48, true, 48, nullptr, &ms);
-      if (rc == EULER_OK && (best < 0.0f || ms < best)) {
-        best = ms;
-        best_min = mins[mi];
+    for (int mi = 0; mi < 4 && rc == EULER_OK; ++mi)
+      for (int ci = 0; ci < 2 && rc == EULER_OK; ++ci) {
+        if (make_batch_plan(b, best_block, best_cap, best_shift, mins[mi], cps[ci]) != EULER_OK) continue;
+        float ms = 0.0f;
+        rc = trial(k_scale, true, true, nullptr, &ms);
+        if (rc == EULER_OK && (best < 0.0f || ms < best)) {
+          best = ms;
+          best_min = mins[mi];
+          best_cp = cps[ci];
+        }
       }
-    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(pool);
   for (euler_net* h : b->nets) cudaMemset(h->d_err, 0, sizeof(unsigned));
   if (rc) return rc;
-  rc = make_batch_plan(b, best_block, best_cap, best_shift, best_min);
+  rc = make_batch_plan(b, best_block, best_cap, best_shift, best_min, best_cp);
   if (rc) return rc;
   if (block_out) *block_out = b->block;
   return EULER_OK;
@@ -463,7 +542,7 @@ int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) tr
   const bool same = !moved && b->exec && b->graph_stats.size() == (size_t)b->count &&
                     std::equal(b->graph_stats.begin(), b->graph_stats.end(), stats);
   if (!same) {
-    int rc = upload_runs(b, stats, 0);
+    int rc = upload_runs(b, stats, 0.0);
     if (rc) return rc;
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
@@ -484,11 +563,25 @@ int euler_batch_run(euler_batch* b, int64_t* const* stats, void* cuda_stream) tr
     b->graph_stats.assign(stats, stats + b->count);
   }
   BTRY(cudaGraphLaunch(b->exec, s));  // zeroes every stats buffer, runs the persistent items
-  return run_hbm_nets(b, stats, s, 0);
+  return run_hbm_nets(b, stats, s, 0.0);
 } catch (const std::bad_alloc&) {
   return bfail(EULER_ERR_OOM, "host memory allocation failed");
 } catch (...) {
   return bfail(EULER_ERR_CUDA, "unexpected error");
+}
+
+int euler_batch_info(const euler_batch* b, int32_t* hbm_networks, int64_t* hbm_min_units,
+                     int32_t* critical_path, int32_t* block, int32_t* tile_shift, int32_t* hbm_block,
+                     int32_t* graph_steps) {
+  if (!b) return bfail(EULER_ERR_ARG, "batch is NULL");
+  if (hbm_networks) *hbm_networks = (int32_t)b->hbm_nets.size();
+  if (hbm_min_units) *hbm_min_units = b->hbm_min_units;
+  if (critical_path) *critical_path = b->cp_factor > 0.0 ? 1 : 0;
+  if (block) *block = b->block;
+  if (tile_shift) *tile_shift = b->rt_shift;
+  if (hbm_block) *hbm_block = b->hbm_block;
+  if (graph_steps) *graph_steps = b->hbm_graph_steps;
+  return EULER_OK;
 }
 
 int euler_batch_status(euler_batch* b, void* cuda_stream) {

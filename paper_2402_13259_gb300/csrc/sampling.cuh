@@ -298,7 +298,7 @@ EN_D float deviance(float x, float m) {  // x ln(x/m) + m - x
     float s = d * v;
     float ej = 2.0f * x * v;
     const float v2 = v * v;
-#pragma unroll
+#pragma unroll 1
     for (int j = 1; j <= 5; ++j) {
       ej = ej * v2;
       s = s + ej / (float)(2 * j + 1);
@@ -318,14 +318,21 @@ EN_D float log_pois_pmf(int k, float lam) {
   return r - deviance(kf, lam);
 }
 
-EN_D float log_binom_pmf(int k, int n, float p, float q) {
+// se_n: stirling_err((float)n), which depends on n only (a BTRS draw computes
+// it once for all its log tests).
+EN_D float log_binom_pmf(int k, int n, float p, float q, float se_n) {
   const float nf = (float)n;
   if (k == 0) return nf * fm::log1p(-p);
   if (k == n) return nf * fm::log(p);
   const float kf = (float)k;
   const float rf = (float)(n - k);
-  const float lc = stirling_err(nf) - stirling_err(kf) - stirling_err(rf) - deviance(kf, nf * p) -
-                   deviance(rf, nf * q);
+  // lc = se_n - d(k) - d(n-k) - bd0(k, np) - bd0(n-k, nq), subtracted in that
+  // order, with one inlined copy of each term's code (smaller kernels)
+  float lc = se_n;
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) lc = lc - stirling_err(t == 0 ? kf : rf);
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) lc = lc - deviance(t == 0 ? kf : rf, t == 0 ? nf * p : nf * q);
   const float lf = fm::kLn2Pi + fm::log(kf) + fm::log1p(-(kf / nf));
   return lc - 0.5f * lf;
 }
@@ -419,17 +426,35 @@ EN_COLD int32_t binomial_btrs(int32_t n, float p, float q, PhiloxStream& st, Sam
   const float alpha = (2.83f + 5.1f / b) * spq;
   int32_t mode = (int32_t)floorf((nf + 1.0f) * p);
   if (mode > n) mode = n;
-  const float lpm = log_binom_pmf(mode, n, p, q);
-  for (int it = 0; it < cx.cap; ++it) {
-    const float u = st.uniform() - 0.5f;
-    const float v = st.uniform();
-    const float us = 0.5f - fabsf(u);
-    const float kf = floorf((2.0f * a / us + b) * u + c);
-    if (kf < 0.0f || kf > nf) continue;
-    const int32_t k = (int32_t)kf;
-    if (us >= 0.07f && v <= vr) return k;
-    const float lv = fm::log(v * alpha / (a / (us * us) + b));
-    if (lv <= log_binom_pmf(k, n, p, q) - lpm) return k;
+  const float se_n = stirling_err(nf);
+  // One inlined copy of the log-pmf serves both its uses: the first pass
+  // evaluates it at the mode (lpm, before any draw, as if computed up
+  // front), every later pass is a rejection iteration that evaluates it at
+  // its candidate k when the squeeze does not accept.
+  float lpm = 0.0f, lv = 0.0f;
+  int32_t kt = mode, k = 0;
+  int it = -1;  // -1: the mode's pass; 0 .. cap-1: rejection iterations
+  for (;;) {
+    if (it >= 0) {
+      if (it >= cx.cap) break;
+      ++it;
+      const float u = st.uniform() - 0.5f;
+      const float v = st.uniform();
+      const float us = 0.5f - fabsf(u);
+      const float kf = floorf((2.0f * a / us + b) * u + c);
+      if (kf < 0.0f || kf > nf) continue;
+      k = (int32_t)kf;
+      if (us >= 0.07f && v <= vr) return k;
+      lv = fm::log(v * alpha / (a / (us * us) + b));
+      kt = k;
+    }
+    const float lp = log_binom_pmf(kt, n, p, q, se_n);
+    if (it < 0) {
+      lpm = lp;
+      it = 0;
+      continue;
+    }
+    if (lv <= lp - lpm) return k;
   }
   cx.err |= kErrSamplerCap;
   return (int32_t)floorf(np);
@@ -512,7 +537,14 @@ EN_COLD float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
     const float u = st.uniform();
     const float x2 = x * x;
     if (u < 1.0f - 0.0331f * (x2 * x2)) return d * v / rate;
-    if (fm::log(u) < 0.5f * x2 + d * ((1.0f - v) + fm::log(v))) return d * v / rate;
+    float lu = 0.0f, lv = 0.0f;  // ln u, ln v from one inlined copy of the logarithm
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {
+      const float l = fm::log(t == 0 ? u : v);
+      if (t == 0) lu = l;
+      else lv = l;
+    }
+    if (lu < 0.5f * x2 + d * ((1.0f - v) + lv)) return d * v / rate;
   }
   cx.err |= kErrSamplerCap;
   return (float)k / rate;

@@ -89,4 +89,5 @@ def test_null_handle_is_an_argument_error(L):
     B = Bd.lib()  # the binding's declared argument types
     assert B.euler_net_simulate_resume(None, 0, 0.01, 1.0, 10, 1, 0, 0, None, None, None, None) == -1
     assert B.euler_net_grad_coupled(None, 0, 0.01, 1.0, 10, 1, 0, 2, 0.05, None, 0, None, None, None) == -1
+    assert B.euler_batch_info(None, None, None, None, None, None, None, None) == -1
     assert isinstance(Bd.lib().euler_net_last_error(), bytes)

@@ -66,8 +66,12 @@ def test_batch_matches_single_runs_and_oracle(Bd, orc):
             out = [s.cpu().numpy() for s in b.run()]
             for j, (x, y) in enumerate(zip(out, single)):
                 assert np.array_equal(x, y), f"run {j} differs from its single launch"
+            assert b.info()["hbm_networks"] == 3  # the three with n R >= 2^18
             blk = b.autotune()
             assert blk in (128, 256, 512)
+            info = b.info()
+            assert info["block"] == blk and info["hbm_block"] in (128, 256) and info["graph_steps"] in (16, 32, 64)
+            assert 0 <= info["hbm_networks"] <= len(runs) and info["tile_shift"] in (-1, 0, 1)
             stats = b.alloc_stats()
             for _ in range(2):  # graph replay on the same buffers
                 b.run(stats)
