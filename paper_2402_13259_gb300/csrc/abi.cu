@@ -225,7 +225,7 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
     if (!is_pow2(Rt) || Rt > 512) return fail(EULER_ERR_ARG, "tile replications must be a power of two <= 512");
   } else {
     for (int cand = 32; cand >= 1; cand >>= 1)
-      if (persistent_smem_bytes(h->n, h->E, cand) <= limit) {
+      if (persistent_smem_bytes(h->n, h->E, h->tables().ring, cand) <= limit) {
         Rt = cand;
         break;
       }
@@ -261,7 +261,7 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
   // level), and its state traffic (about 8 + 8 deg bytes per unit) stays far
   // below HBM bandwidth.  Below the threshold launch gaps dominate.
   if (forced_form <= 0 && (int64_t)h->n * R >= kHbmMinUnitsPerStep) pl->form = 2;
-  if (pl->form == 1 && (Rt < 1 || persistent_smem_bytes(h->n, h->E, Rt) > limit)) {
+  if (pl->form == 1 && (Rt < 1 || persistent_smem_bytes(h->n, h->E, h->tables().ring, Rt) > limit)) {
     if (forced_form == 1) return fail(EULER_ERR_TOO_LARGE, "network tile does not fit in shared memory");
     pl->form = 2;
   }
@@ -290,7 +290,7 @@ int make_plan(euler_net* h, int32_t scheme, int64_t R, Plan* pl) {
     block = (int)std::max<int64_t>(G * Rt, 32);
   }
   pl->block = block;
-  pl->smem = persistent_smem_bytes(h->n, h->E, Rt);
+  pl->smem = persistent_smem_bytes(h->n, h->E, h->tables().ring, Rt);
   pl->num_tiles = (R + Rt - 1) / Rt;
   int per_sm = 0;
   cudaError_t e = persistent_occupancy(scheme, block, (int)pl->smem, &per_sm);
@@ -673,6 +673,11 @@ int euler_net_create(euler_net** out, int32_t n, const int32_t* row_ptr, const i
     euler_net_destroy(h);
     return cuda_fail(e, "euler_net_create upload");
   }
+  rc = ensure_levels(h);  // the slot schedules' levels and ring depth
+  if (rc) {
+    euler_net_destroy(h);
+    return rc;
+  }
   *out = h;
   return EULER_OK;
 } catch (const std::bad_alloc&) {
@@ -960,7 +965,7 @@ int euler_net_grad(euler_net* h, int32_t scheme, double dt, double T, int64_t R,
   int Rt = 32;
   int64_t smem = 0;
   for (; Rt >= 1; Rt /= 2) {
-    smem = persistent_smem_bytes(h->n, h->E, Rt) + grad_smem_extra(h->n, h->n_ex, Rt);
+    smem = persistent_smem_bytes(h->n, h->E, h->tables().ring, Rt) + grad_smem_extra(h->n, h->n_ex, Rt);
     if (smem <= h->smem_optin) break;
   }
   if (Rt < 1) return fail(EULER_ERR_TOO_LARGE, "gradient tile does not fit in shared memory");

@@ -98,7 +98,7 @@ int64_t pow2_floor(int64_t v) {
 }
 
 int64_t state_bytes(const euler_net* h, int64_t Rt) {
-  return 32 * Rt + 4 * ((int64_t)h->n + h->E) * Rt;
+  return 32 * Rt + 4 * ((int64_t)h->n + (int64_t)h->tables().ring * h->E) * Rt;
 }
 
 bool runs_hbm(const euler_batch* b, int j) { return b->is_hbm[j] != 0; }

@@ -115,6 +115,8 @@ struct euler_net {
     t.N0 = N0.empty() ? nullptr : d_N0;
     t.ex_col = d_ex_col;
     t.n_ex = n_ex;
+    t.pos_level = d_pos_level;
+    t.ring = hbm_depth > 2 ? hbm_depth : 2;
     return t;
   }
 };

@@ -25,6 +25,9 @@ struct NetTables {
   const int32_t* N0;           // [n] or nullptr
   const int32_t* ex_col;       // [n] column of the station in the Lambda table, or -1
   int32_t n_ex;                // stations with external arrivals
+  const int32_t* pos_level;    // [n] level of each position of the level order
+  int32_t ring;                // routed-count ring slots of the slot schedules:
+                               // max(2, largest level gap of an edge + 1)
 };
 
 // Per-call parameters.
@@ -66,8 +69,10 @@ inline void set_round_keys(uint32_t* rk, uint32_t key0, uint32_t key1) {
   }
 }
 
-// Shared-memory bytes of the persistent kernel for a tile of `tile_reps`.
-int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps);
+// Shared-memory bytes of the persistent kernel for a tile of `tile_reps`
+// with `ring` slots of routed counts (NetTables::ring for the slot schedules
+// of tile_body, 1 for the step-by-step schedule).
+int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t ring, int32_t tile_reps);
 
 // Batched form: one persistent launch over (network, tile) work items.
 cudaError_t batch_occupancy(int block, int smem, int* blocks_per_sm);

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(512, 2) persistent_kernel(NetTables t, const _
   sm.claim = claim;
   sm.mu_acc = sm.th_acc = nullptr;
   if (GRAD) {
-    const int64_t end = (int64_t)(reinterpret_cast<unsigned char*>(sm.Rs + (int64_t)t.E * Rt) - smem);
+    const int64_t end = (int64_t)(reinterpret_cast<unsigned char*>(sm.Rs + (int64_t)t.ring * t.E * Rt) - smem);
     sm.mu_acc = reinterpret_cast<double*>(smem + (end + 15) / 16 * 16);
     sm.th_acc = sm.mu_acc + (int64_t)n * Rt;
   }
@@ -243,9 +243,9 @@ __global__ void hbm_finish_kernel(NetTables t, RunParams p, HbmState hs, int64_t
 
 }  // namespace
 
-int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t tile_reps) {
+int64_t persistent_smem_bytes(int32_t n, int32_t E, int32_t ring, int32_t tile_reps) {
   return 256 + 6 * 8 * (int64_t)n + 4 * 8 * (int64_t)tile_reps +
-         4 * ((int64_t)n + E) * tile_reps;
+         4 * ((int64_t)n + (int64_t)ring * E) * tile_reps;
 }
 
 namespace {

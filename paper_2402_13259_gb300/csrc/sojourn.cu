@@ -202,7 +202,7 @@ const void* sojourn_fn(int scheme, bool ext) {
 }
 
 int64_t sojourn_smem_bytes(int32_t n, int32_t E, int32_t Rt, int32_t S) {
-  return persistent_smem_bytes(n, E, Rt) + 8 * (int64_t)n * Rt + 12 * (int64_t)S * Rt;
+  return persistent_smem_bytes(n, E, 1, Rt) + 8 * (int64_t)n * Rt + 12 * (int64_t)S * Rt;
 }
 
 int fail(int code, const char* msg) {

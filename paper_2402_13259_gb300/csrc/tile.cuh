@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "sampling.cuh"
@@ -74,6 +75,23 @@ __device__ __forceinline__ void add_scores(const NetTables& t, const RunParams& 
 // Adds per-station sums (and N_K) into sm.sacc and writes the tile's
 // per-replication sums to p.stats.  Ends with a block barrier.
 // rk: the Philox round keys in the kernel's parameter space, or nullptr.
+//
+// Without a hook the loop runs in slots, one block barrier each, with the
+// routed counts in t.ring slots of sm.Rs ([ring][E][Rt]):
+//   backward (Algorithm 2), slot tau = 1 .. K+1: every station gathers its
+//     routed counts of step tau-1 (ring slot (tau-1) % 2) and completes
+//     N_{tau-1}, then draws step tau from it into ring slot tau % 2 -- one
+//     barrier per step instead of two;
+//   forward (Algorithm 3), slot tau = 1 .. K+L-1: the station at level l
+//     runs step tau - l, so its predecessors ran that step and it ran its own
+//     previous step in earlier slots; routed counts of step s stay in ring
+//     slot s % ring until their consumer has read them -- one barrier per
+//     slot instead of one per level and step.
+// Every station's steps still run in order, so the state, the integer sums
+// and each per-(station, replication) score sum are those of the step loop.
+// With a hook (which sees the whole network after each step) the loop runs
+// step by step: a barrier after each phase (backward) or level (forward),
+// routed counts in one slot.
 template <int SCHEME, bool GRAD = false, bool EXT = true, class Hook = NoHook>
 __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p, int64_t tile,
                                           const TileSmem& sm, SamplerCtx& cx, Hook& hook,
@@ -129,6 +147,73 @@ __device__ __forceinline__ void tile_body(const NetTables& t, const RunParams& p
       return __shfl_sync(kFull, s, 0);
     };
 
+    constexpr bool kSlots = std::is_same<Hook, NoHook>::value;
+    if constexpr (kSlots) {
+      const int64_t ring_stride = (int64_t)t.E * Rt;
+      if (SCHEME == 0) {
+        for (int32_t slot = 1; slot <= p.K + 1; ++slot) {
+          const int32_t* rprev = Rs + (int64_t)((slot - 1) & 1) * ring_stride;
+          int32_t* rcur = Rs + (int64_t)(slot & 1) * ring_stride;
+          const float* lam_t = p.lam + (int64_t)(slot <= p.K ? slot - 1 : 0) * t.n_ex;
+          for (int su0 = first_slot(); su0 < n; su0 = next_slot(su0, n)) {
+            const int su = su0 + (g0 - gwarp);
+            const bool act = rvalid && su < n;
+            int32_t v[5] = {0, 0, 0, 0, 0};
+            if (act) {
+              if (slot >= 2) {
+                const int32_t nn = backward_gather(t, su, Ns, rprev, Rt, r, cx.err);
+                const int32_t c = servers_at<EXT>(t, p, su, (uint32_t)(slot - 1));
+                v[0] = nn;
+                v[1] = nn < c ? nn : c;
+                q_r += nn;
+              }
+              if (slot <= p.K) {
+                const UnitOut o = unit_update<false, GRAD, EXT>(t, p, su, (uint32_t)slot, rep, lam_t, Ns, rcur, Rt, r, cx, rk);
+                if (GRAD) add_scores(t, p, sm, su, slot, r, Rt, o);
+                v[2] = o.D;
+                v[3] = o.X;
+                v[4] = o.A;
+                d_r += o.D;
+                x_r += o.X;
+                a_r += o.A;
+              }
+            }
+            reduce_to<5>(sacc + 6 * (int64_t)(su < n ? su : 0), v, lead && su < n, w, shared_station);
+          }
+          ++phase;
+          __syncthreads();
+        }
+      } else {
+        for (int32_t slot = 1; slot <= p.K + t.L - 1; ++slot) {
+          for (int su0 = first_slot(); su0 < n; su0 = next_slot(su0, n)) {
+            const int su = su0 + (g0 - gwarp);
+            const int32_t i = su < n ? __ldg(t.lvl_station + su) : 0;
+            const int32_t tau = su < n ? slot - __ldg(t.pos_level + su) : 0;
+            const bool live = su < n && tau >= 1 && tau <= p.K;
+            int32_t v[5] = {0, 0, 0, 0, 0};
+            if (rvalid && live) {
+              int32_t* redge = Rs + (int64_t)(tau % t.ring) * ring_stride;
+              const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
+              const UnitOut o = unit_update<true, GRAD, EXT>(t, p, i, (uint32_t)tau, rep, lam_t, Ns, redge, Rt, r, cx, rk);
+              if (GRAD) add_scores(t, p, sm, i, tau, r, Rt, o);
+              const int32_t c = servers_at<EXT>(t, p, i, (uint32_t)tau);
+              v[0] = o.N;
+              v[1] = o.N < c ? o.N : c;
+              v[2] = o.D;
+              v[3] = o.X;
+              v[4] = o.A;
+              q_r += o.N;
+              d_r += o.D;
+              x_r += o.X;
+              a_r += o.A;
+            }
+            reduce_to<5>(sacc + 6 * (int64_t)i, v, lead && live, w, shared_station);
+          }
+          ++phase;
+          __syncthreads();
+        }
+      }
+    } else
     for (int32_t tau = 1; tau <= p.K; ++tau) {
       const float* lam_t = p.lam + (int64_t)(tau - 1) * t.n_ex;
       if (SCHEME == 0) {
