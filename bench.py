@@ -37,11 +37,11 @@ METRIC = "station-step updates/s per GB300 (fwd/bwd Euler), % of binding rooflin
 UNIT = "station-step updates/s"
 LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
 # DRAM bytes of one simulate call (mean of the two schemes) from one ncu
-# capture of the step kernels: 11.947 MB (fused backward) and 11.949 MB
+# capture of the step kernels: 11.924 MB (fused backward) and 11.940 MB
 # (skewed forward) per step launch at steady state, x 10,001 and 10,009 step
 # launches per call.  Valid only for the kernel sources with this hash and
 # the launch forms listed; reported as null otherwise.
-TRAFFIC = {"hash": "9f5edef5485b7a91", "forms": [2, 2], "bytes_per_call": 0.5 * (11.947e6 * 10001 + 11.949e6 * 10009)}
+TRAFFIC = {"hash": "cdbed524630e1baa", "forms": [2, 2], "bytes_per_call": 0.5 * (11.924e6 * 10001 + 11.940e6 * 10009)}
 
 
 def sm_count(device: int = 0) -> int:
@@ -620,6 +620,8 @@ def main():
     ap.add_argument("--horizon", type=float, default=0.0, help="horizon T (default 100)")
     ap.add_argument("--form", type=int, default=0,
                     help="launch form of the 100-station workload: 0 = the planner's, 1 = persistent, 2 = HBM")
+    ap.add_argument("--block", type=int, default=0,
+                    help="threads per block of the 100-station workload's kernels (0 = the planner's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -652,6 +654,8 @@ def main():
     h = Bd.EulerNet(run.net)
     if args.form:
         h.set_option(Bd.OPT_FORM, args.form)
+    if args.block:
+        h.set_option(Bd.OPT_BLOCK, args.block)
     stream = torch.cuda.current_stream()
     stats = [torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda") for _ in range(2)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
@@ -726,6 +730,8 @@ def main():
             he = Bd.EulerNet(run.net)
             if args.form:
                 he.set_option(Bd.OPT_FORM, args.form)
+            if args.block:
+                he.set_option(Bd.OPT_BLOCK, args.block)
             for scheme in (0, 1):
                 he.simulate_host(scheme, run.dt, run.T, R, run.seed, rep_begin, out=out[scheme])
             h2d = he.h2d_bytes()
