@@ -427,6 +427,8 @@ def run_single(args):
     n, R = run.net.n, run.R
     K = Bd.num_steps(run.dt, run.T)
     h = Bd.EulerNet(run.net)
+    if args.block:
+        h.set_option(Bd.OPT_BLOCK, args.block)
     stats = torch.empty(Bd.stats_len(n, R), dtype=torch.int64, device="cuda")
     for scheme, name in ((0, "backward"), (1, "forward")):
         if args.workload == "scale":
