@@ -259,16 +259,21 @@ static float stirlerr(float k) {
     t = t + 0.5f * LN_2PI;
     return lfact_small((int)k) - t;
   }
-  float k2 = k * k;
-  float s = (float)(1.0 / 1260.0) / k2;
+  /* 1/(12k) - 1/(360k^3) + 1/(1260k^5), nested in r = 1/k (one division) */
+  float r = 1.0f / k;
+  float r2 = r * r;
+  float s = (float)(1.0 / 1260.0) * r2;
   s = (float)(1.0 / 360.0) - s;
-  s = s / k2;
+  s = s * r2;
   s = (float)(1.0 / 12.0) - s;
-  return s / k;
+  return s * r;
 }
 
 /* bd0(x, m) = x log(x/m) + m - x, by its odd series in v = (x-m)/(x+m) when
- * x is near m (five terms: remaining terms below 1e-8 relative). */
+ * x is near m (five terms: remaining terms below 1e-8 relative); the term of
+ * v^(2j+1) carries 1/(2j+1) as a float constant. */
+static const float inv_odd[6] = {0.0f, (float)(1.0 / 3.0), (float)(1.0 / 5.0), (float)(1.0 / 7.0),
+                                 (float)(1.0 / 9.0), (float)(1.0 / 11.0)};
 static float bd0(float x, float m) {
   if (x == 0.0f) return m;
   float d = x - m;
@@ -279,7 +284,7 @@ static float bd0(float x, float m) {
     float v2 = v * v;
     for (int j = 1; j <= 5; ++j) {
       ej = ej * v2;
-      s = s + ej / (float)(2 * j + 1);
+      s = s + ej * inv_odd[j];
     }
     return s;
   }

@@ -282,27 +282,36 @@ EN_D float stirling_err(float k) {
     t = t + 0.5f * fm::kLn2Pi;
     return log_small_factorial((int)k) - t;
   }
-  const float k2 = k * k;
-  float s = (float)(1.0 / 1260.0) / k2;
+  // 1/(12k) - 1/(360k^3) + 1/(1260k^5), nested in r = 1/k (one division)
+  const float r = 1.0f / k;
+  const float r2 = r * r;
+  float s = (float)(1.0 / 1260.0) * r2;
   s = (float)(1.0 / 360.0) - s;
-  s = s / k2;
+  s = s * r2;
   s = (float)(1.0 / 12.0) - s;
-  return s / k;
+  return s * r;
 }
 
 EN_D float deviance(float x, float m) {  // x ln(x/m) + m - x
   if (x == 0.0f) return m;
   const float d = x - m;
   if (fabsf(d) < 0.1f * (x + m)) {
+    // odd series in v = d/(x+m), five terms, the term of v^(2j+1) times the
+    // float constant 1/(2j+1)
     const float v = d / (x + m);
     float s = d * v;
     float ej = 2.0f * x * v;
     const float v2 = v * v;
-#pragma unroll 1
-    for (int j = 1; j <= 5; ++j) {
-      ej = ej * v2;
-      s = s + ej / (float)(2 * j + 1);
-    }
+    ej = ej * v2;
+    s = s + ej * (float)(1.0 / 3.0);
+    ej = ej * v2;
+    s = s + ej * (float)(1.0 / 5.0);
+    ej = ej * v2;
+    s = s + ej * (float)(1.0 / 7.0);
+    ej = ej * v2;
+    s = s + ej * (float)(1.0 / 9.0);
+    ej = ej * v2;
+    s = s + ej * (float)(1.0 / 11.0);
     return s;
   }
   return x * fm::log(x / m) + m - x;
