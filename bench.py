@@ -37,11 +37,11 @@ METRIC = "station-step updates/s per GB300 (fwd/bwd Euler), % of binding rooflin
 UNIT = "station-step updates/s"
 LANES_PER_SM = 128  # instruction issue: 4 schedulers x 32 lanes per clock
 # DRAM bytes of one simulate call (mean of the two schemes) from one ncu
-# capture of the step kernels: 11.921 MB (fused backward) and 11.933 MB
+# capture of the step kernels: 11.917 MB (fused backward) and 11.938 MB
 # (skewed forward) per step launch at steady state, x 10,001 and 10,009 step
 # launches per call.  Valid only for the kernel sources with this hash and
 # the launch forms listed; reported as null otherwise.
-TRAFFIC = {"hash": "5937538612d177bd", "forms": [2, 2], "bytes_per_call": 0.5 * (11.921e6 * 10001 + 11.933e6 * 10009)}
+TRAFFIC = {"hash": "25feb6e182f56b21", "forms": [2, 2], "bytes_per_call": 0.5 * (11.917e6 * 10001 + 11.938e6 * 10009)}
 
 
 def sm_count(device: int = 0) -> int:

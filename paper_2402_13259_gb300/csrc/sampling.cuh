@@ -156,6 +156,52 @@ EN_HD float log(float x) {
   return fmaf(ef, kLn2Hi, lo);
 }
 
+// fm::exp for an argument known to lie in [-87, 0] (the inversion samplers'
+// starting probabilities e^{-lambda}, lambda < 10, and (1 - p)^n = e^{n ln(1-p)}
+// with n p < 10, p <= 1/2, so n ln(1-p) > -14): the same operations as
+// fm::exp, whose special cases cannot occur there.
+EN_HD float exp_neg(float x) {
+  const float k = floorf(x * kLog2e + 0.5f);
+  float r = fmaf(-k, kLn2Hi, x);
+  r = fmaf(-k, kLn2Lo, r);
+  float s = (float)(1.0 / 5040.0);
+  s = fmaf(s, r, (float)(1.0 / 720.0));
+  s = fmaf(s, r, (float)(1.0 / 120.0));
+  s = fmaf(s, r, (float)(1.0 / 24.0));
+  s = fmaf(s, r, (float)(1.0 / 6.0));
+  s = fmaf(s, r, 0.5f);
+  s = fmaf(s, r, 1.0f);
+  s = fmaf(s, r, 1.0f);
+  return s * bits_f((uint32_t)((int)k + 127) << 23);
+}
+
+// fm::log for an argument known to be a positive normal finite float (every
+// sampler call site but log1p's): the same operations as fm::log, whose
+// special cases (NaN, negative, zero, infinity, subnormal) cannot occur there.
+EN_HD float log_pos(float x) {
+  const uint32_t b = f_bits(x);
+  int e = (int)(b >> 23) - 127;
+  float m = bits_f((b & 0x007fffffu) | 0x3f800000u);
+  if (m > kSqrt2) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  const float f = m - 1.0f;
+  const float s = f / (2.0f + f);
+  const float z = s * s;
+  float t = (float)(1.0 / 9.0);
+  t = fmaf(t, z, (float)(1.0 / 7.0));
+  t = fmaf(t, z, (float)(1.0 / 5.0));
+  t = fmaf(t, z, (float)(1.0 / 3.0));
+  t = t * z;
+  const float sf = s * f;
+  const float corr = fmaf(2.0f * s, t, -sf);
+  const float lm = f + corr;
+  const float ef = (float)e;
+  const float lo = fmaf(ef, kLn2Lo, lm);
+  return fmaf(ef, kLn2Hi, lo);
+}
+
 // e^x - 1: Taylor to degree 8 below ln2/2 in magnitude, else exp(x) - 1.
 EN_HD float expm1(float x) {
   if (fabsf(x) < 0.3465735912322998f) {
@@ -176,6 +222,14 @@ EN_HD float log1p(float x) {
   const float u = 1.0f + x;
   if (u == 1.0f) return x;
   return fm::log(u) * (x / (u - 1.0f));
+}
+
+// fm::log1p for x in [-1/2, 0) (the binomial constants' ln(1 - pe), pe <= 1/2):
+// 1 + x lies in [1/2, 1), so the logarithm's special cases cannot occur.
+EN_HD float log1p_half(float x) {
+  const float u = 1.0f + x;
+  if (u == 1.0f) return x;
+  return fm::log_pos(u) * (x / (u - 1.0f));
 }
 
 }  // namespace fm
@@ -272,12 +326,12 @@ struct SamplerCtx {
 EN_D float log_small_factorial(int k) {  // k <= 9, k! exact in float
   float f = 1.0f;
   for (int j = 2; j <= k; ++j) f = f * (float)j;
-  return fm::log(f);
+  return fm::log_pos(f);  // f in [1, 9!]
 }
 
 EN_D float stirling_err(float k) {
   if (k < 10.0f) {
-    float t = (k + 0.5f) * fm::log(k);
+    float t = (k + 0.5f) * fm::log_pos(k);  // 1 <= k < 10
     t = t - k;
     t = t + 0.5f * fm::kLn2Pi;
     return log_small_factorial((int)k) - t;
@@ -314,14 +368,14 @@ EN_D float deviance(float x, float m) {  // x ln(x/m) + m - x
     s = s + ej * (float)(1.0 / 11.0);
     return s;
   }
-  return x * fm::log(x / m) + m - x;
+  return x * fm::log_pos(x / m) + m - x;  // x >= 1, m >= 10
 }
 
 EN_D float log_pois_pmf(int k, float lam) {
   if (k == 0) return -lam;
   const float kf = (float)k;
-  if (k < 10) return kf * fm::log(lam) - lam - log_small_factorial(k);
-  const float t = fm::kLn2Pi + fm::log(kf);
+  if (k < 10) return kf * fm::log_pos(lam) - lam - log_small_factorial(k);  // lam >= 10
+  const float t = fm::kLn2Pi + fm::log_pos(kf);
   float r = -0.5f * t;
   r = r - stirling_err(kf);
   return r - deviance(kf, lam);
@@ -331,8 +385,8 @@ EN_D float log_pois_pmf(int k, float lam) {
 // it once for all its log tests).
 EN_D float log_binom_pmf(int k, int n, float p, float q, float se_n) {
   const float nf = (float)n;
-  if (k == 0) return nf * fm::log1p(-p);
-  if (k == n) return nf * fm::log(p);
+  if (k == 0) return nf * fm::log1p_half(-p);  // p in (0, 1/2]
+  if (k == n) return nf * fm::log_pos(p);  // n p >= 10, p <= 1/2
   const float kf = (float)k;
   const float rf = (float)(n - k);
   // lc = se_n - d(k) - d(n-k) - bd0(k, np) - bd0(n-k, nq), subtracted in that
@@ -342,7 +396,7 @@ EN_D float log_binom_pmf(int k, int n, float p, float q, float se_n) {
   for (int t = 0; t < 2; ++t) lc = lc - stirling_err(t == 0 ? kf : rf);
 #pragma unroll 1
   for (int t = 0; t < 2; ++t) lc = lc - deviance(t == 0 ? kf : rf, t == 0 ? nf * p : nf * q);
-  const float lf = fm::kLn2Pi + fm::log(kf) + fm::log1p(-(kf / nf));
+  const float lf = fm::kLn2Pi + fm::log_pos(kf) + fm::log1p(-(kf / nf));
   return lc - 0.5f * lf;
 }
 
@@ -365,7 +419,7 @@ EN_COLD int32_t poisson_ptrs(float lam, PhiloxStream& st, SamplerCtx& cx) {
     if (kf < 0.0f || (us < 0.013f && V > us)) continue;
     if (kf > 1.0e9f) continue;
     const int32_t k = (int32_t)kf;
-    const float lhs = fm::log(V * inv_alpha / (a / (us * us) + b));
+    const float lhs = fm::log_pos(V * inv_alpha / (a / (us * us) + b));
     if (lhs <= log_pois_pmf(k, lam)) return k;
   }
   cx.err |= kErrSamplerCap;
@@ -376,7 +430,7 @@ EN_D int32_t poisson(float lam, PhiloxStream& st, SamplerCtx& cx) {
   if (!(lam > 0.0f)) return 0;
   if (EN_LIKELY(lam < 10.0f)) {
     const float u = st.uniform();
-    float p = fm::exp(-lam);
+    float p = fm::exp_neg(-lam);  // 0 < lam < 10
     float F = p;
     int32_t k = 0;
     while (u > F) {
@@ -418,7 +472,7 @@ EN_HD BinomConst binom_const(float p) {
   const float pe = flip ? 1.0f - p : p;
   b.q = 1.0f - pe;
   b.r = pe / b.q;
-  b.lq = fm::log1p(-pe);
+  b.lq = fm::log1p_half(-pe);  // pe in (0, 1/2]
   b.c0 = flip ? -pe : pe;
   return b;
 }
@@ -454,7 +508,7 @@ EN_COLD int32_t binomial_btrs(int32_t n, float p, float q, PhiloxStream& st, Sam
       if (kf < 0.0f || kf > nf) continue;
       k = (int32_t)kf;
       if (us >= 0.07f && v <= vr) return k;
-      lv = fm::log(v * alpha / (a / (us * us) + b));
+      lv = fm::log_pos(v * alpha / (a / (us * us) + b));
       kt = k;
     }
     const float lp = log_binom_pmf(kt, n, p, q, se_n);
@@ -476,7 +530,7 @@ EN_D int32_t binomial_half(int32_t n, float p, float q, float r, float lq, Philo
   const float nf = (float)n;
   const float np = nf * p;
   if (EN_LIKELY(np < 10.0f)) {
-    float pk = fm::exp(nf * lq);
+    float pk = fm::exp_neg(nf * lq);  // n ln(1 - p) > -14 for n p < 10, p <= 1/2
     float F = pk;
     const float u = st.uniform();
     int32_t k = 0;
@@ -514,7 +568,7 @@ EN_D float std_normal(PhiloxStream& st, SamplerCtx& cx) {
     const float v2 = 2.0f * st.uniform() - 1.0f;
     const float s = v1 * v1 + v2 * v2;
     if (s < 1.0f) {
-      const float t = (-2.0f * fm::log(s)) / s;
+      const float t = (-2.0f * fm::log_pos(s)) / s;  // s in [2^-46, 1)
       return v1 * sqrtf(t);
     }
   }
@@ -531,7 +585,7 @@ EN_COLD float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
       const int32_t g = rem < 4 ? rem : 4;
       float prod = st.uniform();
       for (int32_t j = 1; j < g; ++j) prod = prod * st.uniform();
-      S = S - fm::log(prod);
+      S = S - fm::log_pos(prod);  // prod in [2^-96, 1)
       rem = rem - g;
     }
     return S / rate;
@@ -549,7 +603,7 @@ EN_COLD float erlang(int32_t k, float rate, PhiloxStream& st, SamplerCtx& cx) {
     float lu = 0.0f, lv = 0.0f;  // ln u, ln v from one inlined copy of the logarithm
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {
-      const float l = fm::log(t == 0 ? u : v);
+      const float l = fm::log_pos(t == 0 ? u : v);  // u >= 2^-24; v in [2^-72, 2^78]
       if (t == 0) lu = l;
       else lv = l;
     }
