@@ -43,3 +43,24 @@ def test_config_names_the_workload():
     json.dumps(cfg)
     assert "dag100" in cfg["workload"] and cfg["stations"] == 100 and cfg["steps_K"] == 10000
     assert cfg["replications_per_gpu"] == 10000 and "flushed" in cfg["l2"]
+
+
+def test_reference_arm_prints_its_line():
+    """--impl reference times the oracle on the host (no GPU) and prints one
+    JSON line with the headline's metric and unit, its CPU description and an
+    e2e object without copies."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
